@@ -1,0 +1,113 @@
+/*
+ * ccmc_oracle.h -- the CPU oracle's own interface.
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the package's smoke check and the
+ * CPU-baseline leg of the benchmark may load this code.  The CUDA library has
+ * its own, separately written implementation of every step below; the two
+ * share no header, helper, table or constant generator.
+ *
+ * Model (Budrin et al., "The Parallel Monte Carlo Algorithm Implementation on
+ * GPU for the Systems with an Ising Hamiltonian under the Condition of a
+ * Constant Charge Density", Sec. 2.1, Eqs. (1)-(3)):
+ *   an Lx x Ly periodic square lattice, every site in one of four states,
+ *   stored one byte per site, site (x, y) at index y*Lx + x:
+ *     0 : magnetic, s = +1/2 (sigma = +1, S = 0)
+ *     1 : magnetic, s = -1/2 (sigma = -1, S = 0)
+ *     2 : charge S = +1      (sigma = 0)
+ *     3 : charge S = -1      (sigma = 0)
+ *   E = Delta * sum_i S_i^2 + V * sum_<ij> S_i S_j + (J/4) * sum_<ij> sigma_i sigma_j
+ *   with every bond counted once (the right and the down bond of each site),
+ *   and the constraint sum_i S_i = n N (Eq. 2).
+ */
+#ifndef CCMC_ORACLE_H
+#define CCMC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Counter-space tags (fourth counter word) of the independent random streams. */
+#define ORACLE_TAG_SCHED 1u   /* phase schedule (class a0 and offset r)     */
+#define ORACLE_TAG_MOVE 2u    /* per pair: 16-bit u_hi | 16-bit choice      */
+#define ORACLE_TAG_SLOW 3u    /* per pair: u_lo and the choice fallback     */
+#define ORACLE_TAG_FEISTEL 4u /* initial-state placement permutation        */
+#define ORACLE_TAG_SIGN 5u    /* initial spin signs of magnetic sites       */
+#define ORACLE_TAG_SEQ 6u     /* sequential random-pair mode: pair + u_hi   */
+#define ORACLE_TAG_SEQSLOW 7u /* sequential random-pair mode: slow words    */
+
+/* Threshold table: dQ in [-2,2], dBV and dBJ in [-ORACLE_DB, ORACLE_DB]. */
+#define ORACLE_DB 24
+#define ORACLE_NB (2 * ORACLE_DB + 1)
+#define ORACLE_TABLE_SIZE (5 * ORACLE_NB * ORACLE_NB)
+
+/* Observable record: sweeps_done, Nc, BV, BJ, M, M_stag, S_sum, S_stag. */
+#define ORACLE_REC 8
+
+/* Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11). */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Charge counts from (n, c): Q = llround(n N), C = max(llround(c N), |Q|),
+ * C += 1 when C - Q is odd; N+ = (C + Q)/2, N- = (C - Q)/2.  Returns 0, or -1
+ * when C > N or the inputs are not finite. */
+int oracle_charge_counts(int64_t N, double n, double c, int64_t *Q, int64_t *n_plus,
+                         int64_t *n_minus);
+
+/* Rank of site i (0 <= i < N) under the seeded Feistel permutation of [0, N). */
+int64_t oracle_feistel_rank(uint64_t seed, int64_t N, int64_t i);
+
+/* Exact-count initial state: rank < N+ -> S=+1, rank < N+ + N- -> S=-1,
+ * otherwise magnetic with a seeded sign.  Returns 0 or -1 on bad counts. */
+int oracle_init_counts(int Lx, int Ly, uint64_t seed, int64_t n_plus, int64_t n_minus,
+                       uint8_t *st);
+
+/* Acceptance thresholds, ORACLE_TABLE_SIZE entries. */
+void oracle_threshold_table(double beta, double Delta, double V, double J, uint32_t *table);
+int oracle_table_index(int dQ, int dBV, int dBJ);
+
+/* 1 if the offset (rx, ry) is in the allowed set R of the colour schedule. */
+int oracle_offset_allowed(int Lx, int Ly, int rx, int ry);
+/* Schedule of global phase P: class (a0x, a0y) and offset (rx, ry). */
+void oracle_schedule(int Lx, int Ly, uint64_t seed, uint64_t P, int *a0x, int *a0y, int *rx,
+                     int *ry);
+
+/* Integer energy-term changes of moving sites a, b to codes na, nb. */
+void oracle_pair_delta(const uint8_t *st, int Lx, int Ly, int a, int b, int na, int nb,
+                       int out[3]);
+
+/* One coupled-pair Metropolis move on sites a and b.  R is the pair's 32-bit
+ * MOVE word; the SLOW words are drawn from Philox(key, slow_ctr) when needed.
+ * Returns 1 if the lattice changed. */
+int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t R,
+                     const uint32_t key[2], const uint32_t slow_ctr[4], const uint32_t *table);
+
+/* Full recount: out = {Nc, BV, BJ, M, M_stag, S_sum, S_stag}. */
+void oracle_recount(const uint8_t *st, int Lx, int Ly, int64_t out[7]);
+
+/* One colour phase (global phase index P). */
+void oracle_phase(uint8_t *st, int Lx, int Ly, uint64_t seed, uint64_t P, const uint32_t *table);
+
+/* nsweeps colour-ordered sweeps starting at sweep index sweep0; a record is
+ * written after every obs_every-th sweep (obs_every <= 0: none). */
+int64_t oracle_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
+                      int64_t nsweeps, double beta, double Delta, double V, double J,
+                      int obs_every, int64_t *records);
+
+/* Sequential random-pair mode: floor(N/2) moves per sweep, each on a uniform
+ * ordered pair a != b.  Any Lx, Ly >= 2. */
+int64_t oracle_sequential_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
+                                 int64_t nsweeps, double beta, double Delta, double V, double J,
+                                 int obs_every, int64_t *records);
+
+/* Exact enumeration of the states with sum S = Q (N <= 16): histogram over
+ * (Nc, BV, BJ) with bins [Nc][BV + 2N][BJ + 2N] of size (N+1) x (4N+1) x (4N+1);
+ * count, and integer sums of M^2, |M|, M_stag^2 per bin (Lx <= 4).  Returns the
+ * number of states, or -1 for an unsupported shape. */
+int64_t oracle_enumerate(int Lx, int Ly, int Q, int64_t *count, int64_t *m2, int64_t *mabs,
+                         int64_t *mstag2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
