@@ -1,0 +1,132 @@
+/*
+ * ccmc.h -- C ABI of libccmc: the charge-conserving coupled-pair Metropolis
+ * sweep of Budrin et al. ("The Parallel Monte Carlo Algorithm Implementation on
+ * GPU for the Systems with an Ising Hamiltonian under the Condition of a
+ * Constant Charge Density"), on one NVIDIA GB300 (sm_103a).
+ *
+ * Model (Sec. 2.1).  An Lx x Ly square lattice with periodic edges; each site
+ * is magnetic (S = 0, s = +-1/2, sigma = 2 s = +-1) or charged (S = +-1).
+ *   E = Delta sum_i S_i^2 + V sum_<ij> S_i S_j + (J/4) sum_<ij> sigma_i sigma_j
+ * (Eq. 3), every bond counted once, under the constraint sum_i S_i = n N
+ * (Eq. 2), which every move of the library keeps exactly.
+ *
+ * Site codes used by every host buffer of this API (one byte per site, site
+ * (x, y) at index y * Lx + x):
+ *   0 : s = +1/2    1 : s = -1/2    2 : S = +1    3 : S = -1
+ *
+ * Conventions.
+ *   - Return value: CCMC_OK (0) or a negative CCMC_E_* code; ccmc_strerror()
+ *     names it.  A failed call leaves the handle usable unless it returns
+ *     CCMC_E_CUDA, after which only ccmc_*_destroy is meaningful.
+ *   - Memory: the library owns all device memory of a handle (allocated in
+ *     *_create, freed in *_destroy).  The caller owns every host buffer it
+ *     passes; the library never keeps a host pointer after a call returns.
+ *   - Streams: every device operation of a handle is issued on the stream given
+ *     at creation (NULL: a stream the library creates).  Calls that return host
+ *     data synchronise that stream; ccmc_sweep returns as soon as the work is
+ *     queued.  A handle must not be used from two host threads at once.
+ *   - Lx and Ly must be multiples of 4 and at least 4 (the colour schedule
+ *     works on residue classes mod 4), and Lx * Ly <= 2^30.
+ */
+#ifndef CCMC_H
+#define CCMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CCMC_OK 0
+#define CCMC_E_INVAL (-1)   /* bad argument: shape, counts, NaN parameter, ... */
+#define CCMC_E_NOMEM (-2)   /* device or host allocation failed                */
+#define CCMC_E_CUDA (-3)    /* a CUDA runtime call or kernel launch failed     */
+#define CCMC_E_TIMEOUT (-4) /* a bounded device wait gave up                   */
+#define CCMC_E_BUDGET (-5)  /* admission refused: the memory budget is full    */
+#define CCMC_E_STATE (-6)   /* call out of order (e.g. sweep before init)      */
+#define CCMC_E_NOTFOUND (-7)/* unknown ticket or handle                        */
+
+/* Observables after a sweep (Sec. 2.2 and Eq. 3).  All integer terms are exact
+ * recounts of the lattice: Nc = sum S^2, BV = sum_bonds S S, BJ = sum_bonds
+ * sigma sigma, M = sum sigma, M_stag = sum (-1)^(x+y) sigma, S_sum = sum S
+ * (always n N), S_stag = sum (-1)^(x+y) S.  E = Delta Nc + V BV + (J/4) BJ,
+ * evaluated in FP64 on the host with the parameters of the last sweep. */
+typedef struct {
+  int64_t sweeps_done, Nc, BV, BJ, M, M_stag, S_sum, S_stag;
+  double E;
+} ccmc_obs;
+
+typedef struct ccmc_lattice ccmc_lattice;
+
+/* Allocate an Lx x Ly lattice on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL: the library creates one).  The observable ring holds the
+ * last obs_capacity records (<= 0: 4096).  Errors: E_INVAL, E_NOMEM, E_CUDA. */
+int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
+                        ccmc_lattice **out);
+int ccmc_lattice_destroy(ccmc_lattice *h);
+
+/* Constrained initial state (Sec. 3.1, stage 1).  Q = llround(n N);
+ * C = max(llround(charged_frac N), |Q|), plus one when C - Q is odd;
+ * N+ = (C + Q)/2 sites get S = +1 and N- = (C - Q)/2 get S = -1, placed by a
+ * seeded Feistel permutation of the site indices; the remaining sites are
+ * magnetic with seeded random signs.  charged_frac < 0 means 0.3.  Resets the
+ * sweep counter and the observable ring.  Errors: E_INVAL (C > N, NaN). */
+int ccmc_init_constrained(ccmc_lattice *h, uint64_t seed, double n, double charged_frac);
+/* Same placement with explicit counts N+ = n_plus, N- = n_minus. */
+int ccmc_init_counts(ccmc_lattice *h, uint64_t seed, int64_t n_plus, int64_t n_minus);
+
+/* Run nsweeps sweeps of the coupled-pair Metropolis algorithm (Sec. 3.1-3.2)
+ * at inverse temperature beta (k = 1) with couplings Delta, V, J.  A sweep is 8
+ * colour phases; phase P (counted from the initial state) updates every pair
+ * (a, a + r) with a = a0 (mod 4) for a class a0 and an offset r drawn from the
+ * counter-based generator, so no two pairs of a phase interact (the paper's
+ * "map").  After every sweep whose 1-based index is a multiple of obs_every
+ * (<= 0: never) the lattice is recounted into the observable ring.  Results
+ * depend only on (seed, sweep index, site), not on launch shape.
+ * Errors: E_INVAL (beta < 0 or NaN, non-finite couplings), E_STATE. */
+int ccmc_sweep(ccmc_lattice *h, int64_t nsweeps, double beta, double Delta, double V, double J,
+               int obs_every);
+
+/* Recount the current lattice and return its observables (synchronises). */
+int ccmc_observables(ccmc_lattice *h, ccmc_obs *out);
+/* Copy the ring's records, oldest first, into out[0 .. cap); *n_written gets
+ * their number.  Records whose index fell out of the ring are lost. */
+int ccmc_obs_series(ccmc_lattice *h, ccmc_obs *out, int64_t cap, int64_t *n_written);
+
+/* Histograms (per recount in the ring) of M, M_stag and S_stag over nbins
+ * equal bins of [-N, N]: bin = (x + N) nbins / (2N + 1).  Enabling clears
+ * them; out receives 3 * nbins int64 (M, M_stag, S_stag). */
+int ccmc_hist_enable(ccmc_lattice *h, int nbins);
+int ccmc_hist_get(ccmc_lattice *h, int64_t *out);
+
+/* Lattice state as N bytes of site codes (synchronises). */
+int ccmc_get_state(ccmc_lattice *h, uint8_t *host_out);
+/* Load a state (checkpoint / resume): host_in holds N site codes; seed and
+ * sweeps_done fix the random stream, so resuming reproduces the trajectory
+ * bit for bit.  Errors: E_INVAL (code > 3). */
+int ccmc_set_state(ccmc_lattice *h, const uint8_t *host_in, uint64_t seed, int64_t sweeps_done);
+
+/* Block until the handle's queued work is done; reports a device-side error. */
+int ccmc_sync(ccmc_lattice *h);
+
+/* Host-only: the acceptance thresholds the sweep uses (Sec. 3.1, "otherwise
+ * the classical Metropolis algorithm"), for dQ in {-2, 0, 2} and dBV, dBJ in
+ * [-20, 20]: out[((dQ + 2)/2 * 41 + dBV + 20) * 41 + dBJ + 20] =
+ * 0xFFFFFFFF if dE <= 0, else min(floor(2^32 exp(-beta dE)), 0xFFFFFFFE), with
+ * dE = Delta dQ + V dBV + (J/4) dBJ in FP64.  A move is accepted iff its
+ * threshold is 0xFFFFFFFF or a uniform 32-bit word is below it.  out holds
+ * 5043 entries.  No GPU needed. */
+int ccmc_threshold_table(double beta, double Delta, double V, double J, uint32_t *out);
+
+/* Diagnostic: Philox4x32-10 on the device for counters (c0 + i, c1, c2, c3),
+ * i < count, key (k0, k1); out receives 4 * count words (host buffer). */
+int ccmc_philox_device(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                       uint32_t k1, int64_t count, uint32_t *out);
+
+const char *ccmc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

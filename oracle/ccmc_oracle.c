@@ -360,9 +360,10 @@ static void write_record(const uint8_t *st, int Lx, int Ly, int64_t sweeps_done,
 
 /* ------------------------------------------------------------------------ */
 /* One colour phase: every pair (a, a + r), a = (4i + a0x, 4j + a0y), with pair
- * index k = j * (Lx/4) + i inside the class.  Pair k takes word k mod 4 of
- * Philox(seed, (k/4, P_lo, P_hi, MOVE)) and its slow words from
- * Philox(seed, (k, P_lo, P_hi, SLOW)). */
+ * index k = j * (Lx/4) + i inside the class.  Pairs come in groups of four
+ * consecutive i of one class row: pair (i, j) takes word i mod 4 of
+ * Philox(seed, (j * ceil(Lx/16) + i/4, P_lo, P_hi, MOVE)), and its slow words
+ * from Philox(seed, (k, P_lo, P_hi, SLOW)). */
 void oracle_phase(uint8_t *st, int Lx, int Ly, uint64_t seed, uint64_t P, const uint32_t *table) {
   uint32_t key[2];
   seed_key(seed, key);
@@ -375,10 +376,11 @@ void oracle_phase(uint8_t *st, int Lx, int Ly, uint64_t seed, uint64_t P, const 
       int64_t k = (int64_t)j * Cx + i;
       int ax = 4 * i + a0x, ay = 4 * j + a0y;
       int bx = (ax + rx) % Lx, by = (ay + ry) % Ly;
-      uint32_t mctr[4] = {(uint32_t)(k >> 2), Plo, Phi, ORACLE_TAG_MOVE};
+      int64_t group = (int64_t)j * ((Cx + 3) / 4) + i / 4;
+      uint32_t mctr[4] = {(uint32_t)group, Plo, Phi, ORACLE_TAG_MOVE};
       uint32_t mw[4];
       oracle_philox4x32_10(mctr, key, mw);
-      uint32_t R = mw[k & 3];
+      uint32_t R = mw[i & 3];
       uint32_t sctr[4] = {(uint32_t)k, Plo, Phi, ORACLE_TAG_SLOW};
       oracle_pair_move(st, Lx, Ly, ay * Lx + ax, by * Lx + bx, R, key, sctr, table);
     }

@@ -1,0 +1,186 @@
+"""Python binding of libccmc: the charge-conserving coupled-pair Metropolis
+sweep (Budrin et al.) on one GB300.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``libccmc.so`` behind the C ABI of ``include/ccmc.h``.  The library must have
+been built (``__graft_entry__.build()`` or ``python -m
+paper_2301_11735_gb300.build``); importing this package without it raises.
+
+Site codes of every host array: 0: s=+1/2, 1: s=-1/2, 2: S=+1, 3: S=-1, as a
+``uint8`` array of shape (Ly, Lx).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int64, c_uint32, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libccmc.so")
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUDGET, E_STATE, E_NOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
+TABLE_N = 3 * 41 * 41
+OBS_FIELDS = ("sweeps_done", "Nc", "BV", "BJ", "M", "M_stag", "S_sum", "S_stag", "E")
+
+
+class CcmcError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {_lib.ccmc_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [(n, c_int64) for n in OBS_FIELDS[:-1]] + [("E", c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n in OBS_FIELDS}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+            "(the package has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64p, u32p, u8p = c_void_p, POINTER(c_int64), POINTER(c_uint32), POINTER(ctypes.c_uint8)
+    sigs = {
+        "ccmc_strerror": (ctypes.c_char_p, [c_int]),
+        "ccmc_threshold_table": (c_int, [c_double, c_double, c_double, c_double, u32p]),
+        "ccmc_lattice_create": (c_int, [c_int, c_int, vp, c_int64, POINTER(vp)]),
+        "ccmc_lattice_destroy": (c_int, [vp]),
+        "ccmc_init_constrained": (c_int, [vp, c_uint64, c_double, c_double]),
+        "ccmc_init_counts": (c_int, [vp, c_uint64, c_int64, c_int64]),
+        "ccmc_sweep": (c_int, [vp, c_int64, c_double, c_double, c_double, c_double, c_int]),
+        "ccmc_observables": (c_int, [vp, POINTER(Obs)]),
+        "ccmc_obs_series": (c_int, [vp, POINTER(Obs), c_int64, i64p]),
+        "ccmc_hist_enable": (c_int, [vp, c_int]),
+        "ccmc_hist_get": (c_int, [vp, i64p]),
+        "ccmc_get_state": (c_int, [vp, u8p]),
+        "ccmc_set_state": (c_int, [vp, u8p, c_uint64, c_int64]),
+        "ccmc_sync": (c_int, [vp]),
+        "ccmc_philox_device": (c_int, [c_uint32] * 6 + [c_int64, u32p]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise CcmcError(code, what)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return c_void_p(stream.cuda_stream)
+    return c_void_p(int(stream))
+
+
+def threshold_table(beta: float, Delta: float, V: float, J: float) -> np.ndarray:
+    """The library's acceptance thresholds, shape (3, 41, 41) = [dQ/2 + 1, dBV + 20, dBJ + 20]."""
+    out = np.zeros(TABLE_N, dtype=np.uint32)
+    _check(_lib.ccmc_threshold_table(beta, Delta, V, J, out.ctypes.data_as(POINTER(c_uint32))),
+           "ccmc_threshold_table")
+    return out.reshape(3, 41, 41)
+
+
+def philox_device(ctr, key, count: int) -> np.ndarray:
+    """Device Philox4x32-10 of counters (ctr[0] + i, ctr[1], ctr[2], ctr[3])."""
+    out = np.zeros(4 * count, dtype=np.uint32)
+    _check(_lib.ccmc_philox_device(*[int(c) & 0xFFFFFFFF for c in ctr],
+                                   *[int(k) & 0xFFFFFFFF for k in key], count,
+                                   out.ctypes.data_as(POINTER(c_uint32))), "ccmc_philox_device")
+    return out.reshape(count, 4)
+
+
+class Lattice:
+    """An Lx x Ly lattice resident on the current CUDA device."""
+
+    def __init__(self, Lx: int, Ly: int, stream=None, obs_capacity: int = 4096):
+        self.Lx, self.Ly = int(Lx), int(Ly)
+        h = c_void_p()
+        _check(_lib.ccmc_lattice_create(self.Lx, self.Ly, _stream_handle(stream), obs_capacity,
+                                        ctypes.byref(h)), "ccmc_lattice_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ccmc_lattice_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init_constrained(self, seed: int, n: float, charged_frac: float = 0.3):
+        _check(_lib.ccmc_init_constrained(self._h, seed & (2 ** 64 - 1), n, charged_frac),
+               "ccmc_init_constrained")
+
+    def init_counts(self, seed: int, n_plus: int, n_minus: int):
+        _check(_lib.ccmc_init_counts(self._h, seed & (2 ** 64 - 1), n_plus, n_minus),
+               "ccmc_init_counts")
+
+    def sweep(self, nsweeps: int, beta: float, Delta: float, V: float, J: float,
+              obs_every: int = 0):
+        _check(_lib.ccmc_sweep(self._h, nsweeps, beta, Delta, V, J, obs_every), "ccmc_sweep")
+
+    def sync(self):
+        _check(_lib.ccmc_sync(self._h), "ccmc_sync")
+
+    def observables(self) -> dict:
+        o = Obs()
+        _check(_lib.ccmc_observables(self._h, ctypes.byref(o)), "ccmc_observables")
+        return o.as_dict()
+
+    def obs_series(self, cap: int = 1 << 20) -> np.ndarray:
+        """int64 records (sweeps_done, Nc, BV, BJ, M, M_stag, S_sum, S_stag), oldest first."""
+        buf = (Obs * cap)()
+        n = c_int64()
+        _check(_lib.ccmc_obs_series(self._h, buf, cap, ctypes.byref(n)), "ccmc_obs_series")
+        out = np.zeros((n.value, 8), dtype=np.int64)
+        for r in range(n.value):
+            out[r] = [getattr(buf[r], f) for f in OBS_FIELDS[:-1]]
+        return out
+
+    def hist_enable(self, nbins: int):
+        _check(_lib.ccmc_hist_enable(self._h, nbins), "ccmc_hist_enable")
+        self._nbins = nbins
+
+    def hist(self) -> np.ndarray:
+        out = np.zeros(3 * self._nbins, dtype=np.int64)
+        _check(_lib.ccmc_hist_get(self._h, out.ctypes.data_as(POINTER(c_int64))), "ccmc_hist_get")
+        return out.reshape(3, self._nbins)
+
+    def get_state(self) -> np.ndarray:
+        out = np.zeros((self.Ly, self.Lx), dtype=np.uint8)
+        _check(_lib.ccmc_get_state(self._h, out.ctypes.data_as(POINTER(ctypes.c_uint8))),
+               "ccmc_get_state")
+        return out
+
+    def set_state(self, st: np.ndarray, seed: int, sweeps_done: int = 0):
+        st = np.ascontiguousarray(st, dtype=np.uint8)
+        assert st.shape == (self.Ly, self.Lx)
+        _check(_lib.ccmc_set_state(self._h, st.ctypes.data_as(POINTER(ctypes.c_uint8)),
+                                   seed & (2 ** 64 - 1), sweeps_done), "ccmc_set_state")

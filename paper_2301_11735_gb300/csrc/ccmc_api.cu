@@ -1,0 +1,466 @@
+// ccmc_api.cu -- the C ABI of libccmc (declared in include/ccmc.h): handle
+// lifecycle, parameter tables, the sweep driver and state transfer.  Host code
+// only; the kernels live in ccmc_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ccmc.h"
+#include "ccmc_internal.h"
+
+using namespace ccmc;
+
+#define CK(call)                                \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return CCMC_E_CUDA;  \
+  } while (0)
+
+namespace {
+
+// A sweep of the graph path is captured as a chunk of `sweeps` sweeps; with
+// obs_every in [1, 16] the chunk holds a recount after every obs_every-th
+// sweep and is replayed only when the run is aligned to obs_every.
+struct GraphEntry {
+  int sweeps = 0;
+  int obs_every = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+
+constexpr int kChunk = 16;
+
+}  // namespace
+
+struct ccmc_lattice {
+  Geo g{};
+  int h = 1;  // Feistel half width: 4^h >= N
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  uint32_t *d_words = nullptr;
+  int64_t *d_ctl = nullptr;
+  int64_t *d_partials = nullptr;
+  int64_t *d_ring = nullptr;
+  int64_t ring_cap = 0;
+  int64_t *d_hist = nullptr;
+  int nbins = 0;
+  void *d_tables = nullptr;
+  DevTables t{};
+  uint8_t *d_bytes = nullptr;
+  int *d_flag = nullptr;
+  bool initialised = false;
+  uint64_t seed = 0;
+  int64_t sweeps_done = 0;
+  bool have_params = false;
+  double params[4] = {0, 0, 0, 0};  // beta, Delta, V, J
+  LaunchCfg cfg{};
+  std::vector<GraphEntry> graphs;
+};
+
+namespace {
+
+int validate_shape(int Lx, int Ly) {
+  if (Lx < 4 || Ly < 4 || (Lx & 3) || (Ly & 3)) return CCMC_E_INVAL;
+  if ((int64_t)Lx * (int64_t)Ly > ((int64_t)1 << 30)) return CCMC_E_INVAL;
+  return CCMC_OK;
+}
+
+void set_seed(ccmc_lattice *h, uint64_t seed) {
+  h->seed = seed;
+  h->g.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
+  h->g.k1 = (uint32_t)(seed >> 32);
+}
+
+void drop_graphs(ccmc_lattice *h) {
+  for (auto &e : h->graphs)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  h->graphs.clear();
+}
+
+int upload_params(ccmc_lattice *h, double beta, double Delta, double V, double J) {
+  if (h->have_params && h->params[0] == beta && h->params[1] == Delta && h->params[2] == V &&
+      h->params[3] == J)
+    return CCMC_OK;
+  std::vector<uint32_t> thr32(kTableN);
+  std::vector<uint16_t> thr16(kTableN);
+  build_thresholds(beta, Delta, V, J, thr32.data());
+  for (int i = 0; i < kTableN; ++i) thr16[i] = (uint16_t)(thr32[i] >> 16);
+  CK(cudaMemcpyAsync(h->t.thr32, thr32.data(), sizeof(uint32_t) * kTableN,
+                     cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->t.thr16, thr16.data(), sizeof(uint16_t) * kTableN,
+                     cudaMemcpyHostToDevice, h->stream));
+  // pageable sources: the copies are staged before the calls return
+  h->have_params = true;
+  h->params[0] = beta;
+  h->params[1] = Delta;
+  h->params[2] = V;
+  h->params[3] = J;
+  return CCMC_OK;
+}
+
+// Queue `sweeps` sweeps starting at phase offset 0 of the control block's base;
+// obs_every > 0: a recount after every obs_every-th of them (the caller aligns).
+int enqueue_chunk(ccmc_lattice *h, int sweeps, int obs_every) {
+  for (int s = 0; s < sweeps; ++s) {
+    for (int p = 0; p < 8; ++p) CK(launch_phase(h->g, h->t, 8LL * s + p, h->cfg, h->stream));
+    if (obs_every > 0 && (s + 1) % obs_every == 0)
+      CK(launch_recount(h->g, h->d_partials, h->d_ring, h->ring_cap, h->d_hist, h->nbins, s + 1,
+                        h->stream));
+  }
+  CK(launch_advance(h->d_ctl, 8LL * sweeps, h->stream));
+  return CCMC_OK;
+}
+
+int run_graph(ccmc_lattice *h, int sweeps, int obs_every) {
+  GraphEntry *hit = nullptr;
+  for (auto &e : h->graphs)
+    if (e.sweeps == sweeps && e.obs_every == obs_every) hit = &e;
+  if (!hit) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_chunk(h, sweeps, obs_every);
+    const cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+    if (rc != CCMC_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return CCMC_E_CUDA;
+    }
+    GraphEntry e;
+    e.sweeps = sweeps;
+    e.obs_every = obs_every;
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return CCMC_E_CUDA;
+    h->graphs.push_back(e);
+    hit = &h->graphs.back();
+  }
+  CK(cudaGraphLaunch(hit->exec, h->stream));
+  return CCMC_OK;
+}
+
+int write_recount_latest(ccmc_lattice *h) {
+  CK(launch_recount(h->g, h->d_partials, nullptr, 0, nullptr, 0, 0, h->stream));
+  return CCMC_OK;
+}
+
+void fill_obs(const ccmc_lattice *h, const int64_t *rec, ccmc_obs *o) {
+  o->sweeps_done = rec[0];
+  o->Nc = rec[1];
+  o->BV = rec[2];
+  o->BJ = rec[3];
+  o->M = rec[4];
+  o->M_stag = rec[5];
+  o->S_sum = rec[6];
+  o->S_stag = rec[7];
+  const double Delta = h->params[1], V = h->params[2], J = h->params[3];
+  o->E = Delta * (double)rec[1] + V * (double)rec[2] + (0.25 * J) * (double)rec[3];
+}
+
+int check_status(ccmc_lattice *h) {
+  int64_t st = 0;
+  CK(cudaMemcpyAsync(&st, h->d_ctl + kCtlStatus, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return st == 0 ? CCMC_OK : CCMC_E_TIMEOUT;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ccmc_strerror(int code) {
+  switch (code) {
+    case CCMC_OK: return "ok";
+    case CCMC_E_INVAL: return "invalid argument";
+    case CCMC_E_NOMEM: return "out of memory";
+    case CCMC_E_CUDA: return "CUDA error";
+    case CCMC_E_TIMEOUT: return "device wait timed out";
+    case CCMC_E_BUDGET: return "memory budget exhausted";
+    case CCMC_E_STATE: return "call out of order";
+    case CCMC_E_NOTFOUND: return "not found";
+    default: return "unknown error";
+  }
+}
+
+int ccmc_threshold_table(double beta, double Delta, double V, double J, uint32_t *out) {
+  if (!out || !(beta >= 0.0) || !std::isfinite(Delta) || !std::isfinite(V) ||
+      !std::isfinite(J))
+    return CCMC_E_INVAL;
+  build_thresholds(beta, Delta, V, J, out);
+  return CCMC_OK;
+}
+
+int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
+                        ccmc_lattice **out) {
+  if (!out) return CCMC_E_INVAL;
+  *out = nullptr;
+  int rc = validate_shape(Lx, Ly);
+  if (rc) return rc;
+  ccmc_lattice *h = new (std::nothrow) ccmc_lattice();
+  if (!h) return CCMC_E_NOMEM;
+  Geo &g = h->g;
+  g.Lx = Lx;
+  g.Ly = Ly;
+  g.Cx = Lx / 4;
+  g.Cy = Ly / 4;
+  g.W = (g.Cx + 15) / 16;
+  g.Cx4 = (g.Cx + 3) / 4;
+  g.cstride = (int64_t)g.Cy * g.W;
+  const uint64_t N = (uint64_t)Lx * (uint64_t)Ly;
+  g.rej = (0 - N) % N;
+  while (((int64_t)1 << (2 * h->h)) < (int64_t)N) ++h->h;
+  h->ring_cap = obs_capacity > 0 ? obs_capacity : 4096;
+  cudaGetDevice(&h->device);
+  auto fail = [&](int code) {
+    ccmc_lattice_destroy(h);
+    return code;
+  };
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(CCMC_E_CUDA);
+    h->own_stream = true;
+  }
+  const int np = recount_grid(g);
+  if (cudaMalloc(&h->d_words, sizeof(uint32_t) * 16 * g.cstride) != cudaSuccess ||
+      cudaMalloc(&h->d_ctl, sizeof(int64_t) * kCtlWords) != cudaSuccess ||
+      cudaMalloc(&h->d_partials, sizeof(int64_t) * 7 * np) != cudaSuccess ||
+      cudaMalloc(&h->d_ring, sizeof(int64_t) * 8 * h->ring_cap) != cudaSuccess ||
+      cudaMalloc(&h->d_flag, sizeof(int)) != cudaSuccess)
+    return fail(CCMC_E_NOMEM);
+  const size_t tb = sizeof(uint32_t) * kTableN + sizeof(uint16_t) * kTableN + 16 +
+                    2 * sizeof(int32_t) * 256;
+  if (cudaMalloc(&h->d_tables, tb) != cudaSuccess) return fail(CCMC_E_NOMEM);
+  char *p = (char *)h->d_tables;
+  h->t.thr32 = (uint32_t *)p;
+  p += sizeof(uint32_t) * kTableN;
+  h->t.trans_far = (int32_t *)p;
+  p += sizeof(int32_t) * 256;
+  h->t.trans_near = (int32_t *)p;
+  p += sizeof(int32_t) * 256;
+  h->t.thr16 = (uint16_t *)p;
+  g.words = h->d_words;
+  g.ctl = h->d_ctl;
+  int32_t tf[256], tn[256];
+  build_transitions(tf, tn);
+  if (cudaMemcpyAsync(h->t.trans_far, tf, sizeof(tf), cudaMemcpyHostToDevice, h->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(h->t.trans_near, tn, sizeof(tn), cudaMemcpyHostToDevice, h->stream) !=
+          cudaSuccess ||
+      cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t) * 16 * g.cstride, h->stream) !=
+          cudaSuccess ||
+      launch_set_ctl(h->d_ctl, 0, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return fail(CCMC_E_CUDA);
+  *out = h;
+  return CCMC_OK;
+}
+
+int ccmc_lattice_destroy(ccmc_lattice *h) {
+  if (!h) return CCMC_E_INVAL;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  cudaFree(h->d_words);
+  cudaFree(h->d_ctl);
+  cudaFree(h->d_partials);
+  cudaFree(h->d_ring);
+  cudaFree(h->d_hist);
+  cudaFree(h->d_tables);
+  cudaFree(h->d_bytes);
+  cudaFree(h->d_flag);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return CCMC_OK;
+}
+
+int ccmc_init_counts(ccmc_lattice *h, uint64_t seed, int64_t n_plus, int64_t n_minus) {
+  if (!h) return CCMC_E_INVAL;
+  const int64_t N = (int64_t)h->g.Lx * h->g.Ly;
+  if (n_plus < 0 || n_minus < 0 || n_plus + n_minus > N) return CCMC_E_INVAL;
+  set_seed(h, seed);
+  CK(launch_set_ctl(h->d_ctl, 0, h->stream));
+  CK(launch_init(h->g, h->h, n_plus, n_minus, h->stream));
+  if (h->d_hist) CK(cudaMemsetAsync(h->d_hist, 0, sizeof(int64_t) * 3 * h->nbins, h->stream));
+  h->sweeps_done = 0;
+  h->initialised = true;
+  CK(cudaStreamSynchronize(h->stream));
+  return CCMC_OK;
+}
+
+int ccmc_init_constrained(ccmc_lattice *h, uint64_t seed, double n, double charged_frac) {
+  if (!h) return CCMC_E_INVAL;
+  if (!std::isfinite(n)) return CCMC_E_INVAL;
+  if (charged_frac < 0.0) charged_frac = 0.3;
+  if (!std::isfinite(charged_frac)) return CCMC_E_INVAL;
+  const int64_t N = (int64_t)h->g.Lx * h->g.Ly;
+  const int64_t Q = std::llround(n * (double)N);
+  int64_t C = std::llround(charged_frac * (double)N);
+  const int64_t aQ = Q < 0 ? -Q : Q;
+  if (C < aQ) C = aQ;
+  if ((C - Q) & 1) C += 1;
+  if (C > N) return CCMC_E_INVAL;
+  return ccmc_init_counts(h, seed, (C + Q) / 2, (C - Q) / 2);
+}
+
+int ccmc_sweep(ccmc_lattice *h, int64_t nsweeps, double beta, double Delta, double V, double J,
+               int obs_every) {
+  if (!h || nsweeps < 0) return CCMC_E_INVAL;
+  if (!(beta >= 0.0) || !std::isfinite(Delta) || !std::isfinite(V) || !std::isfinite(J))
+    return CCMC_E_INVAL;
+  if (!h->initialised) return CCMC_E_STATE;
+  int rc = upload_params(h, beta, Delta, V, J);
+  if (rc) return rc;
+  int64_t s = 0;
+  while (s < nsweeps) {
+    const int64_t abs_sweep = h->sweeps_done + s;
+    const int64_t remaining = nsweeps - s;
+    if (obs_every > 0 && obs_every <= kChunk) {
+      const int g = obs_every * (kChunk / obs_every);
+      if (abs_sweep % obs_every == 0 && remaining >= g) {
+        rc = run_graph(h, g, obs_every);
+        if (rc) return rc;
+        s += g;
+        continue;
+      }
+    } else {
+      const int64_t dist = obs_every > 0 ? obs_every - abs_sweep % obs_every : INT64_MAX;
+      if (remaining >= kChunk && dist > kChunk) {
+        rc = run_graph(h, kChunk, 0);
+        if (rc) return rc;
+        s += kChunk;
+        continue;
+      }
+    }
+    // one sweep, launched directly
+    for (int p = 0; p < 8; ++p) CK(launch_phase(h->g, h->t, p, h->cfg, h->stream));
+    if (obs_every > 0 && (abs_sweep + 1) % obs_every == 0)
+      CK(launch_recount(h->g, h->d_partials, h->d_ring, h->ring_cap, h->d_hist, h->nbins, 1,
+                        h->stream));
+    CK(launch_advance(h->d_ctl, 8, h->stream));
+    s += 1;
+  }
+  h->sweeps_done += nsweeps;
+  return CCMC_OK;
+}
+
+int ccmc_sync(ccmc_lattice *h) {
+  if (!h) return CCMC_E_INVAL;
+  return check_status(h);
+}
+
+int ccmc_observables(ccmc_lattice *h, ccmc_obs *out) {
+  if (!h || !out) return CCMC_E_INVAL;
+  if (!h->initialised) return CCMC_E_STATE;
+  int rc = write_recount_latest(h);
+  if (rc) return rc;
+  int64_t rec[8];
+  CK(cudaMemcpyAsync(rec, h->d_ctl + kCtlLatest, sizeof(rec), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  rec[0] = h->sweeps_done;
+  fill_obs(h, rec, out);
+  return check_status(h);
+}
+
+int ccmc_obs_series(ccmc_lattice *h, ccmc_obs *out, int64_t cap, int64_t *n_written) {
+  if (!h || !n_written || cap < 0 || (cap > 0 && !out)) return CCMC_E_INVAL;
+  int64_t cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, h->d_ctl + kCtlObsCount, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int64_t held = cnt < h->ring_cap ? cnt : h->ring_cap;
+  const int64_t first = cnt - held;
+  std::vector<int64_t> ring((size_t)(8 * h->ring_cap));
+  CK(cudaMemcpyAsync(ring.data(), h->d_ring, sizeof(int64_t) * 8 * h->ring_cap,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int64_t n = 0;
+  for (int64_t r = first; r < cnt && n < cap; ++r, ++n)
+    fill_obs(h, ring.data() + 8 * (r % h->ring_cap), out + n);
+  *n_written = n;
+  return CCMC_OK;
+}
+
+int ccmc_hist_enable(ccmc_lattice *h, int nbins) {
+  if (!h || nbins < 1 || nbins > (1 << 20)) return CCMC_E_INVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  drop_graphs(h);  // captured recounts hold the old histogram pointer
+  cudaFree(h->d_hist);
+  h->d_hist = nullptr;
+  h->nbins = 0;
+  if (cudaMalloc(&h->d_hist, sizeof(int64_t) * 3 * nbins) != cudaSuccess) return CCMC_E_NOMEM;
+  h->nbins = nbins;
+  CK(cudaMemsetAsync(h->d_hist, 0, sizeof(int64_t) * 3 * nbins, h->stream));
+  return CCMC_OK;
+}
+
+int ccmc_hist_get(ccmc_lattice *h, int64_t *out) {
+  if (!h || !out) return CCMC_E_INVAL;
+  if (!h->d_hist) return CCMC_E_STATE;
+  CK(cudaMemcpyAsync(out, h->d_hist, sizeof(int64_t) * 3 * h->nbins, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CCMC_OK;
+}
+
+static int ensure_bytes(ccmc_lattice *h) {
+  if (h->d_bytes) return CCMC_OK;
+  const size_t N = (size_t)h->g.Lx * h->g.Ly;
+  if (cudaMalloc(&h->d_bytes, N) != cudaSuccess) return CCMC_E_NOMEM;
+  return CCMC_OK;
+}
+
+int ccmc_get_state(ccmc_lattice *h, uint8_t *host_out) {
+  if (!h || !host_out) return CCMC_E_INVAL;
+  if (!h->initialised) return CCMC_E_STATE;
+  int rc = ensure_bytes(h);
+  if (rc) return rc;
+  const size_t N = (size_t)h->g.Lx * h->g.Ly;
+  CK(launch_unpack(h->g, h->d_bytes, h->stream));
+  CK(cudaMemcpyAsync(host_out, h->d_bytes, N, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CCMC_OK;
+}
+
+int ccmc_set_state(ccmc_lattice *h, const uint8_t *host_in, uint64_t seed, int64_t sweeps_done) {
+  if (!h || !host_in || sweeps_done < 0) return CCMC_E_INVAL;
+  int rc = ensure_bytes(h);
+  if (rc) return rc;
+  const size_t N = (size_t)h->g.Lx * h->g.Ly;
+  int zero = 0, bad = 0;
+  CK(cudaMemcpyAsync(h->d_flag, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_bytes, host_in, N, cudaMemcpyHostToDevice, h->stream));
+  set_seed(h, seed);
+  CK(launch_pack(h->g, h->d_bytes, h->d_flag, h->stream));
+  CK(launch_set_ctl(h->d_ctl, 8 * sweeps_done, h->stream));
+  if (h->d_hist) CK(cudaMemsetAsync(h->d_hist, 0, sizeof(int64_t) * 3 * h->nbins, h->stream));
+  CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (bad) {
+    h->initialised = false;
+    return CCMC_E_INVAL;
+  }
+  h->sweeps_done = sweeps_done;
+  h->initialised = true;
+  return CCMC_OK;
+}
+
+int ccmc_philox_device(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                       uint32_t k1, int64_t count, uint32_t *out) {
+  if (!out || count < 0 || count > ((int64_t)1 << 28)) return CCMC_E_INVAL;
+  if (count == 0) return CCMC_OK;
+  uint32_t *d = nullptr;
+  if (cudaMalloc(&d, sizeof(uint32_t) * 4 * count) != cudaSuccess) return CCMC_E_NOMEM;
+  int rc = CCMC_OK;
+  if (launch_philox(c0, c1, c2, c3, k0, k1, count, d, 0) != cudaSuccess ||
+      cudaMemcpy(out, d, sizeof(uint32_t) * 4 * count, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = CCMC_E_CUDA;
+  cudaFree(d);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// ccmc_device.cuh -- device building blocks of the coupled-pair Metropolis
+// sweep (Budrin et al., Sec. 3): counter-based random numbers, the packed
+// lattice layout, the colour schedule and the per-pair move.
+//
+// Packed layout.  Site (x, y) belongs to residue class (x mod 4, y mod 4) and
+// sits at column i = x / 4, row j = y / 4 of that class's Cy x Cx grid
+// (Cx = Lx / 4, Cy = Ly / 4).  Each class row is stored as W = ceil(Cx / 16)
+// 32-bit words, 16 sites per word, site i at bits 2 (i mod 16) .. +1 of word
+// i / 16; the 16 classes are stored one after another (class c = 4 (y mod 4) +
+// (x mod 4)).  A colour phase updates all pairs (a, a + r) with a in one class:
+// the a-sites of one word are 16 pairs whose partners, and all their
+// neighbours, are 16 consecutive sites of other class rows -- fetched as one
+// shifted word ("window").
+#pragma once
+
+#include <cstdint>
+
+#include "ccmc_internal.h"
+
+namespace ccmc {
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies whose halves are cross-mixed with the key, the key advancing by
+// the two Weyl constants between rounds.
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    c0 = hi1 ^ c1 ^ k0;
+    c2 = hi0 ^ c3 ^ k1;
+    c1 = lo1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ uint32_t *row_ptr(const Geo &g, int cls, int row) {
+  return g.words + (int64_t)cls * g.cstride + (int64_t)row * g.W;
+}
+
+// n (<= 16) consecutive sites of a class row starting at column `start`
+// (periodic in the row), site t at bits 2t .. 2t+1.  Bits beyond 2n are
+// unspecified.
+__device__ __forceinline__ uint32_t fetch_window(const uint32_t *row, int W, int Cx, int start,
+                                                 int n) {
+  const int wi = start >> 4, o = start & 15;
+  const uint32_t lo = row[wi];
+  const uint32_t hi = row[(wi + 1 < W) ? wi + 1 : 0];
+  uint32_t v = __funnelshift_r(lo, hi, 2 * o);
+  const int n1 = Cx - start;  // sites left before the row wraps
+  if (n1 < n) v = (v & ((1u << (2 * n1)) - 1u)) | (row[0] << (2 * n1));
+  return v;
+}
+
+// XOR the first n sites of D into the class row at column `start` (periodic).
+// Only bits of the caller's own sites are nonzero, so concurrent XORs from other
+// threads into the same words commute.
+__device__ __forceinline__ void scatter_xor(uint32_t *row, int Cx, int start, int n, uint32_t D) {
+  if (D == 0u) return;
+  const int n1 = min(n, Cx - start);
+  const uint32_t d1 = (n1 < 16) ? (D & ((1u << (2 * n1)) - 1u)) : D;
+  const int wi = start >> 4, o = start & 15;
+  if (d1) {
+    atomicXor(row + wi, d1 << (2 * o));
+    if (o) {
+      const uint32_t h = d1 >> (32 - 2 * o);
+      if (h) atomicXor(row + wi + 1, h);
+    }
+  }
+  if (n1 < n) {
+    const uint32_t d2 = D >> (2 * n1);
+    if (d2) atomicXor(row, d2);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Colour schedule of global phase P (Sec. 3.2, a "map" of non-interacting
+// pairs): attempt t draws Philox(seed, (t, P_lo, P_hi, SCHED)); class a0 from
+// the low 4 bits of word 0 and the offset index from words 1-2 by Lemire's
+// multiply-high with rejection; the first attempt whose offset is allowed wins.
+struct Sched {
+  int a0x, a0y, rx, ry;
+  int near;  // r is an exact nearest-neighbour offset: the pair shares a bond
+};
+
+__device__ __forceinline__ bool offset_allowed(int Lx, int Ly, int rx, int ry) {
+  if (rx == 0 && ry == 0) return false;
+  if (ry == 0 && (rx == 1 || rx == Lx - 1)) return true;
+  if (rx == 0 && (ry == 1 || ry == Ly - 1)) return true;
+  const int mx = rx & 3, my = ry & 3;
+  if (mx == 0 && my == 0) return false;
+  if (my == 0 && (mx & 1)) return false;
+  if (mx == 0 && (my & 1)) return false;
+  return true;
+}
+
+// Executed by one full warp; every lane returns the same schedule.
+__device__ __forceinline__ Sched draw_schedule(const Geo &g, uint64_t P) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t N = (uint64_t)g.Lx * (uint64_t)g.Ly;
+  Sched s{0, 0, 2, 2, 0};
+  for (uint32_t base = 0; base < 64; base += 32) {
+    const U4 w = philox(base + lane, (uint32_t)P, (uint32_t)(P >> 32), TAG_SCHED, g.k0, g.k1);
+    const uint64_t x = ((uint64_t)w.z << 32) | (uint64_t)w.y;
+    const uint64_t lo = x * N;
+    const uint64_t idx = __umul64hi(x, N);
+    const int rx = (int)(idx % (uint64_t)g.Lx);
+    const int ry = (int)(idx / (uint64_t)g.Lx);
+    const bool ok = (lo >= g.rej) && offset_allowed(g.Lx, g.Ly, rx, ry);
+    const unsigned ballot = __ballot_sync(0xFFFFFFFFu, ok);
+    if (ballot) {
+      const int src = __ffs(ballot) - 1;
+      s.a0x = __shfl_sync(0xFFFFFFFFu, (int)(w.x & 3u), src);
+      s.a0y = __shfl_sync(0xFFFFFFFFu, (int)((w.x >> 2) & 3u), src);
+      s.rx = __shfl_sync(0xFFFFFFFFu, rx, src);
+      s.ry = __shfl_sync(0xFFFFFFFFu, ry, src);
+      break;
+    }
+  }
+  s.near = (s.ry == 0 && (s.rx == 1 || s.rx == g.Lx - 1)) ||
+           (s.rx == 0 && (s.ry == 1 || s.ry == g.Ly - 1));
+  return s;
+}
+
+// ----------------------------------------------------------------------------
+// Pair move (Sec. 3.1).  A pair state is pc = 4 code_a + code_b.
+//   QCLASS: 2 bits per pc: 0 = frozen (q = +-2), 1 = q = +1, 2 = q = 0, 3 = q = -1.
+//   SET_*:  the q-set in the paper's order, one 4-bit pc per entry.
+constexpr uint32_t kQClass = (2u << 0) | (2u << 2) | (1u << 4) | (3u << 6) |  // a = +1/2
+                             (2u << 8) | (2u << 10) | (1u << 12) | (3u << 14) |  // a = -1/2
+                             (1u << 16) | (1u << 18) | (0u << 20) | (2u << 22) |  // a = +1
+                             (3u << 24) | (3u << 26) | (2u << 28) | (0u << 30);   // a = -1
+constexpr uint32_t kSetP = 8u | (9u << 4) | (2u << 8) | (6u << 12);    // q = +1
+constexpr uint32_t kSetM = 12u | (13u << 4) | (3u << 8) | (7u << 12);  // q = -1
+constexpr uint32_t kSet0 = 11u | (14u << 4) | (0u << 8) | (5u << 12) | (1u << 16) | (4u << 20);
+
+// Transition entry for (pc -> npc), built on the host: bits 0-12 base index
+// (dQ class, biases, and for neighbouring pairs the a-b bond term), bits 13-20
+// 41 * dS_a (signed), bits 21-24 dsigma_a, bits 25-28 dsigma_b (signed).  The
+// threshold index is base + (41 dS_a) (SA - SB) + dsig_a GA + dsig_b GB with
+// SA = sum_<a> S + 4, GA = sum_<a> sigma + 4 (and likewise for b).
+__device__ __forceinline__ int trans_index(int32_t e, int sa4, int sb4, int ga4, int gb4) {
+  const uint32_t u = (uint32_t)e;
+  const int base = (int)(u & 0x1FFFu);
+  const int mulS = (int)(u << 11) >> 24;
+  const int dga = (int)(u << 7) >> 28;
+  const int dgb = (int)(u << 3) >> 28;
+  return base + mulS * (sa4 - sb4) + dga * ga4 + dgb * gb4;
+}
+
+// Biased neighbour sums of 16 sites held in four neighbour windows, as two
+// words of 4-bit lanes (even sites, odd sites): lane = sum (S + 1) over the
+// four neighbours (in [0, 8]); likewise for sigma.
+struct Sums {
+  uint32_t se, so, ge, go;
+};
+
+__device__ __forceinline__ void add_neighbour(Sums &s, uint32_t X) {
+  const uint32_t K = (X >> 1) & 0x55555555u;  // charged
+  const uint32_t G = X & 0x55555555u;         // sign bit (1 = negative)
+  const uint32_t nK = ~K & 0x55555555u;
+  // S + 1 = 2 (S = +1), 1 (magnetic), 0 (S = -1); sigma + 1 likewise.
+  const uint32_t s1 = ((K & ~G) << 1) | nK;
+  const uint32_t g1 = ((nK & ~G) << 1) | K;
+  s.se += s1 & 0x33333333u;
+  s.so += (s1 >> 2) & 0x33333333u;
+  s.ge += g1 & 0x33333333u;
+  s.go += (g1 >> 2) & 0x33333333u;
+}
+
+__device__ __forceinline__ int lane4(uint32_t even, uint32_t odd, int t) {
+  return (int)((((t & 1) ? odd : even) >> (4 * (t >> 1))) & 15u);
+}
+
+}  // namespace ccmc

@@ -1,0 +1,72 @@
+// ccmc_internal.h -- library-internal types shared by the host API and the
+// kernels (plain C++, no device code).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ccmc {
+
+constexpr uint32_t TAG_SCHED = 1u;    // phase schedule
+constexpr uint32_t TAG_MOVE = 2u;     // per 4-pair group: u_hi | choice
+constexpr uint32_t TAG_SLOW = 3u;     // per pair: u_lo, choice fallback
+constexpr uint32_t TAG_FEISTEL = 4u;  // initial placement
+constexpr uint32_t TAG_SIGN = 5u;     // initial spin signs
+
+constexpr int kDB = 20;                 // |dBV|, |dBJ| <= 20 when Lx, Ly >= 4
+constexpr int kNB = 2 * kDB + 1;        // 41
+constexpr int kTableN = 3 * kNB * kNB;  // dQ in {-2, 0, 2}: 5043 thresholds
+
+// Control block of a lattice (int64 words in device memory).
+enum CtlSlot : int {
+  kCtlPhaseBase = 0,  // global phase index of the next phase with offset 0
+  kCtlObsCount = 1,   // records written to the ring so far
+  kCtlTicket = 2,     // arrival counter of the recount's last-block reduction
+  kCtlStatus = 3,     // device-side error flag
+  kCtlLatest = 4,     // 8 words: the last recount record
+  kCtlWords = 16
+};
+
+// Lattice geometry as seen by the kernels.
+struct Geo {
+  uint32_t *words;  // 16 classes x Cy rows x W words
+  int64_t *ctl;     // control block
+  int Lx, Ly, Cx, Cy, W;
+  int Cx4;          // ceil(Cx / 4): 4-pair groups per class row
+  int64_t cstride;  // Cy * W words per class
+  uint32_t k0, k1;  // Philox key = seed
+  uint64_t rej;     // 2^64 mod (Lx Ly): Lemire rejection bound
+};
+
+// Per-lattice parameter tables in device memory (built on the host).
+struct DevTables {
+  uint16_t *thr16;     // kTableN: high 16 bits of each threshold
+  uint32_t *thr32;     // kTableN: full thresholds
+  int32_t *trans_far;  // 256: transition entries, partner not a neighbour
+  int32_t *trans_near; // 256: transition entries, partner a nearest neighbour
+};
+
+struct LaunchCfg {
+  int phase_grid_cap = 152 * 8;
+};
+
+// Host-side table builders (ccmc_tables.cpp).
+void build_thresholds(double beta, double Delta, double V, double J, uint32_t *thr32);
+void build_transitions(int32_t *trans_far, int32_t *trans_near);
+
+// Launchers (ccmc_kernels.cu).
+cudaError_t launch_init(const Geo &g, int h, int64_t n_plus, int64_t n_minus, cudaStream_t s);
+cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const LaunchCfg &cfg,
+                         cudaStream_t s);
+int recount_grid(const Geo &g);
+cudaError_t launch_recount(const Geo &g, int64_t *partials, int64_t *ring, int64_t ring_cap,
+                           int64_t *hist, int nbins, int64_t sweep_off, cudaStream_t s);
+cudaError_t launch_advance(int64_t *ctl, int64_t phases, cudaStream_t s);
+cudaError_t launch_set_ctl(int64_t *ctl, int64_t phase_base, cudaStream_t s);
+cudaError_t launch_unpack(const Geo &g, uint8_t *out, cudaStream_t s);
+cudaError_t launch_pack(const Geo &g, const uint8_t *in, int *bad, cudaStream_t s);
+cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                          uint32_t k1, int64_t count, uint32_t *out, cudaStream_t s);
+
+}  // namespace ccmc

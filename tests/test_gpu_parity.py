@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Every comparison is bit-exact: lattice states, integer energy terms, the
+charge sum (which must equal n N after every sweep), schedules and random
+words.  Shapes cover several tiles of 16 sites, ragged row tails (Lx/4 not a
+multiple of 16 or of 4), rows shorter than one word, and the full sizes of the
+4096^2 and 16384^2 workloads (sampled or single-sweep there).
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+from .gpu_util import first_difference, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(4, 4), (8, 8), (12, 20), (16, 16), (20, 12), (36, 44), (64, 64), (68, 20), (80, 72),
+          (128, 128), (132, 8), (260, 36)]
+PARAMS = [(1.0, 0.5, 1.0, 1.0), (1 / 0.6, 0.2, 1.0, 0.5), (5.0, 0.0, 0.5, 1.0),
+          (0.5, -0.5, 1.0, 1.0), (1 / 3.0, -1.0, 2.0, 1.0)]
+
+
+@pytest.fixture(scope="module")
+def cc():
+    import paper_2301_11735_gb300 as cc
+
+    return cc
+
+
+def test_device_philox_matches_oracle(cc):
+    for ctr, key in [((0, 0, 0, 0), (0, 0)), ((0xFFFFFF00, 7, 9, 2), (0xDEADBEEF, 0x12345678)),
+                     ((123, 0xFFFFFFFF, 0, 5), (1, 0))]:
+        dev = cc.philox_device(ctr, key, 300)
+        for i in range(0, 300, 7):
+            c = [(ctr[0] + i) & 0xFFFFFFFF, ctr[1], ctr[2], ctr[3]]
+            assert np.array_equal(dev[i], oracle.philox(c, key)), (ctr, key, i)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_initial_state_matches_oracle(cc, shape):
+    Lx, Ly = shape
+    N = Lx * Ly
+    with cc.Lattice(Lx, Ly) as lat:
+        for seed, (npl, nmi) in [(1, (N // 5, N // 10)), (2 ** 40 + 3, (0, 0)), (99, (N, 0)),
+                                 (7, (N // 3, N // 3))]:
+            lat.init_counts(seed, npl, nmi)
+            got = lat.get_state()
+            exp = oracle.init_counts(Lx, Ly, seed, npl, nmi)
+            assert np.array_equal(got, exp), (shape, seed, first_difference(got, exp))
+        lat.init_constrained(11, 0.1, 0.3)
+        assert np.array_equal(lat.get_state(), oracle.init_constrained(Lx, Ly, 11, 0.1, 0.3))
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (20, 12), (68, 20), (128, 128)])
+def test_state_roundtrip_and_bad_codes(cc, shape):
+    Lx, Ly = shape
+    rng = np.random.default_rng(3)
+    st = rng.integers(0, 4, size=(Ly, Lx)).astype(np.uint8)
+    with cc.Lattice(Lx, Ly) as lat:
+        lat.set_state(st, 5, 0)
+        assert np.array_equal(lat.get_state(), st)
+        obs = lat.observables()
+        assert [obs[k] for k in ("Nc", "BV", "BJ", "M", "M_stag", "S_sum", "S_stag")] == \
+            list(oracle.recount(st))
+        bad = st.copy()
+        bad[0, 0] = 4
+        with pytest.raises(cc.CcmcError):
+            lat.set_state(bad, 5, 0)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("params", PARAMS[:3])
+def test_sweeps_bit_exact_every_sweep(cc, shape, params):
+    Lx, Ly = shape
+    beta, Delta, V, J = params
+    seed = 1000 + Lx * 7 + Ly
+    st0 = oracle.init_constrained(Lx, Ly, seed, 0.1, 0.3)
+    Q = int(oracle.recount(st0)[5])
+    with cc.Lattice(Lx, Ly) as lat:
+        lat.init_constrained(seed, 0.1, 0.3)
+        st = st0.copy()
+        for s in range(6):
+            lat.sweep(1, beta, Delta, V, J, obs_every=1)
+            st, rec = oracle_run(st, seed, s, 1, beta, Delta, V, J)
+            got = lat.get_state()
+            assert np.array_equal(got, st), (shape, s, first_difference(got, st))
+            assert oracle.recount(got)[5] == Q
+        recs = lat.obs_series()
+        assert len(recs) == 6 and np.all(recs[:, 6] == Q)
+        assert np.array_equal(recs[-1], rec[-1])
+
+
+@pytest.mark.parametrize("params", PARAMS)
+def test_multi_sweep_calls_graph_and_direct_paths(cc, params):
+    """Long calls run through captured CUDA graphs, short or misaligned ones
+    launch directly; both must give the oracle's records at every obs point."""
+    beta, Delta, V, J = params
+    Lx, Ly, seed = 36, 44, 77
+    st = oracle.init_constrained(Lx, Ly, seed, -0.05, 0.4)
+    with cc.Lattice(Lx, Ly, obs_capacity=512) as lat:
+        lat.init_constrained(seed, -0.05, 0.4)
+        done = 0
+        all_rec = []
+        for n, every in [(37, 1), (5, 3), (40, 3), (33, 0), (50, 7), (41, 20)]:
+            lat.sweep(n, beta, Delta, V, J, obs_every=every)
+            st, rec = oracle_run(st, seed, done, n, beta, Delta, V, J, obs_every=every)
+            all_rec.append(rec)
+            done += n
+            got = lat.get_state()
+            assert np.array_equal(got, st), (n, every, first_difference(got, st))
+        exp = np.concatenate([r for r in all_rec if len(r)])
+        assert np.array_equal(lat.obs_series(), exp)
+
+
+def test_workload_16x16_full_length(cc):
+    """L = 16, Delta = 0.5, V = J = 1, T = 1, 48 charges +1 and 16 charges -1,
+    2000 sweeps with observables after every sweep: identical records."""
+    seed = 1
+    st = oracle.init_counts(16, 16, seed, 48, 16)
+    _, rec = oracle_run(st, seed, 0, 2000, 1.0, 0.5, 1.0, 1.0, obs_every=1)
+    with cc.Lattice(16, 16) as lat:
+        lat.init_counts(seed, 48, 16)
+        lat.sweep(2000, 1.0, 0.5, 1.0, 1.0, obs_every=1)
+        got = lat.obs_series()
+    assert np.all(got[:, 6] == 32)
+    assert np.array_equal(got, rec)
+
+
+@pytest.mark.parametrize("params", [(0.0, 1.0, 1.0, 1.0), (float("inf"), 0.5, 1.0, 1.0),
+                                    (1.0, 1e9, 1.0, 1.0), (1.0, -1e9, 1.0, 1.0)])
+@pytest.mark.parametrize("shape", [(16, 16), (20, 12)])
+def test_degenerate_parameters(cc, params, shape):
+    Lx, Ly = shape
+    beta, Delta, V, J = params
+    st = oracle.init_counts(Lx, Ly, 5, Lx * Ly // 8 + 4, Lx * Ly // 8)
+    with cc.Lattice(Lx, Ly) as lat:
+        lat.init_counts(5, Lx * Ly // 8 + 4, Lx * Ly // 8)
+        lat.sweep(30, beta, Delta, V, J, obs_every=1)
+        st, rec = oracle_run(st, 5, 0, 30, beta, Delta, V, J)
+        assert np.array_equal(lat.get_state(), st)
+        assert np.array_equal(lat.obs_series(), rec)
+
+
+def test_checkpoint_resume_is_bit_exact(cc):
+    Lx = Ly = 64
+    with cc.Lattice(Lx, Ly) as a, cc.Lattice(Lx, Ly) as b:
+        a.init_constrained(9, 0.1, 0.3)
+        a.sweep(100, 1.2, 0.2, 1.0, 0.5, obs_every=10)
+        b.init_constrained(9, 0.1, 0.3)
+        b.sweep(50, 1.2, 0.2, 1.0, 0.5, obs_every=10)
+        snap = b.get_state()
+        b.init_counts(123, 1, 1)  # scramble, then restore
+        b.set_state(snap, 9, 50)
+        b.sweep(50, 1.2, 0.2, 1.0, 0.5, obs_every=10)
+        assert np.array_equal(a.get_state(), b.get_state())
+        assert np.array_equal(a.obs_series()[-5:], b.obs_series()[-5:])
+
+
+def test_histograms_follow_the_records(cc):
+    Lx = Ly = 32
+    N = Lx * Ly
+    nb = 64
+    with cc.Lattice(Lx, Ly) as lat:
+        lat.hist_enable(nb)
+        lat.init_constrained(4, 0.05, 0.3)
+        lat.sweep(200, 1 / 0.6, 0.2, 1.0, 0.5, obs_every=1)
+        rec = lat.obs_series()
+        h = lat.hist()
+    for row, col in enumerate((4, 5, 7)):
+        bins = (rec[:, col] + N) * nb // (2 * N + 1)
+        assert np.array_equal(h[row], np.bincount(bins, minlength=nb))
+
+
+@pytest.mark.parametrize("T", [0.5, 2.0])
+def test_full_size_4096_first_sweeps(cc, T):
+    """The 4096^2 workload (Delta = 0, V = 0.5, J = 1, n = 0.1, charged
+    fraction 0.3): identical initial state and identical lattice and records
+    after each of the first three sweeps."""
+    L, seed = 4096, 20
+    st = oracle.init_constrained(L, L, seed, 0.1, 0.3)
+    with cc.Lattice(L, L) as lat:
+        lat.init_constrained(seed, 0.1, 0.3)
+        assert np.array_equal(lat.get_state(), st)
+        for s in range(3):
+            lat.sweep(1, 1.0 / T, 0.0, 0.5, 1.0, obs_every=1)
+            st, rec = oracle_run(st, seed, s, 1, 1.0 / T, 0.0, 0.5, 1.0)
+            assert np.array_equal(lat.get_state(), st), s
+        assert np.array_equal(lat.obs_series()[-1], rec[-1])
+        assert rec[-1][6] == 1677722
+
+
+def test_full_size_16384_sampled_init_and_one_sweep(cc):
+    """The 16384^2 workload: the initial state is checked on sampled sites
+    (oracle rank of each sampled site), then one GPU sweep from that state is
+    compared with one oracle sweep from the same state."""
+    L, seed = 16384, 5
+    N = L * L
+    Q, npl, nmi = oracle.charge_counts(N, 0.05, 0.3)
+    with cc.Lattice(L, L) as lat:
+        lat.init_constrained(seed, 0.05, 0.3)
+        st = lat.get_state()
+        counts = np.bincount(st.ravel(), minlength=4)
+        assert counts[2] == npl and counts[3] == nmi
+        rng = np.random.default_rng(0)
+        key = oracle.seed_key(seed)
+        for i in rng.integers(0, N, size=2000):
+            r = oracle.feistel_rank(seed, N, int(i))
+            if r < npl:
+                exp = 2
+            elif r < npl + nmi:
+                exp = 3
+            else:
+                w = oracle.philox([int(i) >> 7, 0, 0, oracle.TAG_SIGN], key)
+                exp = int((w[(int(i) >> 5) & 3] >> (int(i) & 31)) & 1)
+            assert st.flat[i] == exp, i
+        lat.sweep(1, 1 / 0.6, 0.2, 1.0, 0.5, obs_every=1)
+        got = lat.get_state()
+        oracle_run_state, rec = oracle_run(st, seed, 0, 1, 1 / 0.6, 0.2, 1.0, 0.5)
+        assert np.array_equal(got, oracle_run_state)
+        assert np.array_equal(lat.obs_series()[-1], rec[-1])
+        assert rec[-1][6] == Q
