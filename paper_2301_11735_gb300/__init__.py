@@ -4,7 +4,8 @@ sweep (Budrin et al.) on one GB300.
 Argument marshalling only: every step of the method runs in the CUDA kernels of
 ``libccmc.so`` behind the C ABI of ``include/ccmc.h``.  The library must have
 been built (``__graft_entry__.build()`` or ``python -m
-paper_2301_11735_gb300.build``); importing this package without it raises.
+paper_2301_11735_gb300.build``); the first call into the package raises
+ImportError when it is missing -- there is no CPU fallback.
 
 Site codes of every host array: 0: s=+1/2, 1: s=-1/2, 2: S=+1, 3: S=-1, as a
 ``uint8`` array of shape (Ly, Lx).
@@ -27,7 +28,7 @@ OBS_FIELDS = ("sweeps_done", "Nc", "BV", "BJ", "M", "M_stag", "S_sum", "S_stag",
 
 class CcmcError(RuntimeError):
     def __init__(self, code: int, what: str):
-        super().__init__(f"{what}: {_lib.ccmc_strerror(code).decode()} ({code})")
+        super().__init__(f"{what}: {lib().ccmc_strerror(code).decode()} ({code})")
         self.code = code
 
 
@@ -69,10 +70,14 @@ def _load():
     return lib
 
 
-_lib = _load()
+_lib = None
 
 
 def lib():
+    """The loaded libccmc (loaded on first use; ImportError if it was not built)."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
     return _lib
 
 
@@ -92,7 +97,7 @@ def _stream_handle(stream):
 def threshold_table(beta: float, Delta: float, V: float, J: float) -> np.ndarray:
     """The library's acceptance thresholds, shape (3, 41, 41) = [dQ/2 + 1, dBV + 20, dBJ + 20]."""
     out = np.zeros(TABLE_N, dtype=np.uint32)
-    _check(_lib.ccmc_threshold_table(beta, Delta, V, J, out.ctypes.data_as(POINTER(c_uint32))),
+    _check(lib().ccmc_threshold_table(beta, Delta, V, J, out.ctypes.data_as(POINTER(c_uint32))),
            "ccmc_threshold_table")
     return out.reshape(3, 41, 41)
 
@@ -100,7 +105,7 @@ def threshold_table(beta: float, Delta: float, V: float, J: float) -> np.ndarray
 def philox_device(ctr, key, count: int) -> np.ndarray:
     """Device Philox4x32-10 of counters (ctr[0] + i, ctr[1], ctr[2], ctr[3])."""
     out = np.zeros(4 * count, dtype=np.uint32)
-    _check(_lib.ccmc_philox_device(*[int(c) & 0xFFFFFFFF for c in ctr],
+    _check(lib().ccmc_philox_device(*[int(c) & 0xFFFFFFFF for c in ctr],
                                    *[int(k) & 0xFFFFFFFF for k in key], count,
                                    out.ctypes.data_as(POINTER(c_uint32))), "ccmc_philox_device")
     return out.reshape(count, 4)
@@ -112,7 +117,7 @@ class Lattice:
     def __init__(self, Lx: int, Ly: int, stream=None, obs_capacity: int = 4096):
         self.Lx, self.Ly = int(Lx), int(Ly)
         h = c_void_p()
-        _check(_lib.ccmc_lattice_create(self.Lx, self.Ly, _stream_handle(stream), obs_capacity,
+        _check(lib().ccmc_lattice_create(self.Lx, self.Ly, _stream_handle(stream), obs_capacity,
                                         ctypes.byref(h)), "ccmc_lattice_create")
         self._h = h
 
@@ -122,7 +127,7 @@ class Lattice:
 
     def close(self):
         if getattr(self, "_h", None):
-            _lib.ccmc_lattice_destroy(self._h)
+            lib().ccmc_lattice_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -135,52 +140,50 @@ class Lattice:
         self.close()
 
     def init_constrained(self, seed: int, n: float, charged_frac: float = 0.3):
-        _check(_lib.ccmc_init_constrained(self._h, seed & (2 ** 64 - 1), n, charged_frac),
+        _check(lib().ccmc_init_constrained(self._h, seed & (2 ** 64 - 1), n, charged_frac),
                "ccmc_init_constrained")
 
     def init_counts(self, seed: int, n_plus: int, n_minus: int):
-        _check(_lib.ccmc_init_counts(self._h, seed & (2 ** 64 - 1), n_plus, n_minus),
+        _check(lib().ccmc_init_counts(self._h, seed & (2 ** 64 - 1), n_plus, n_minus),
                "ccmc_init_counts")
 
     def sweep(self, nsweeps: int, beta: float, Delta: float, V: float, J: float,
               obs_every: int = 0):
-        _check(_lib.ccmc_sweep(self._h, nsweeps, beta, Delta, V, J, obs_every), "ccmc_sweep")
+        _check(lib().ccmc_sweep(self._h, nsweeps, beta, Delta, V, J, obs_every), "ccmc_sweep")
 
     def sync(self):
-        _check(_lib.ccmc_sync(self._h), "ccmc_sync")
+        _check(lib().ccmc_sync(self._h), "ccmc_sync")
 
     def observables(self) -> dict:
         o = Obs()
-        _check(_lib.ccmc_observables(self._h, ctypes.byref(o)), "ccmc_observables")
+        _check(lib().ccmc_observables(self._h, ctypes.byref(o)), "ccmc_observables")
         return o.as_dict()
 
     def obs_series(self, cap: int = 1 << 20) -> np.ndarray:
         """int64 records (sweeps_done, Nc, BV, BJ, M, M_stag, S_sum, S_stag), oldest first."""
         buf = (Obs * cap)()
         n = c_int64()
-        _check(_lib.ccmc_obs_series(self._h, buf, cap, ctypes.byref(n)), "ccmc_obs_series")
-        out = np.zeros((n.value, 8), dtype=np.int64)
-        for r in range(n.value):
-            out[r] = [getattr(buf[r], f) for f in OBS_FIELDS[:-1]]
-        return out
+        _check(lib().ccmc_obs_series(self._h, buf, cap, ctypes.byref(n)), "ccmc_obs_series")
+        raw = np.frombuffer(buf, dtype=np.int64).reshape(cap, 9)  # 8 int64 + the double E
+        return raw[:n.value, :8].copy()
 
     def hist_enable(self, nbins: int):
-        _check(_lib.ccmc_hist_enable(self._h, nbins), "ccmc_hist_enable")
+        _check(lib().ccmc_hist_enable(self._h, nbins), "ccmc_hist_enable")
         self._nbins = nbins
 
     def hist(self) -> np.ndarray:
         out = np.zeros(3 * self._nbins, dtype=np.int64)
-        _check(_lib.ccmc_hist_get(self._h, out.ctypes.data_as(POINTER(c_int64))), "ccmc_hist_get")
+        _check(lib().ccmc_hist_get(self._h, out.ctypes.data_as(POINTER(c_int64))), "ccmc_hist_get")
         return out.reshape(3, self._nbins)
 
     def get_state(self) -> np.ndarray:
         out = np.zeros((self.Ly, self.Lx), dtype=np.uint8)
-        _check(_lib.ccmc_get_state(self._h, out.ctypes.data_as(POINTER(ctypes.c_uint8))),
+        _check(lib().ccmc_get_state(self._h, out.ctypes.data_as(POINTER(ctypes.c_uint8))),
                "ccmc_get_state")
         return out
 
     def set_state(self, st: np.ndarray, seed: int, sweeps_done: int = 0):
         st = np.ascontiguousarray(st, dtype=np.uint8)
         assert st.shape == (self.Ly, self.Lx)
-        _check(_lib.ccmc_set_state(self._h, st.ctypes.data_as(POINTER(ctypes.c_uint8)),
+        _check(lib().ccmc_set_state(self._h, st.ctypes.data_as(POINTER(ctypes.c_uint8)),
                                    seed & (2 ** 64 - 1), sweeps_done), "ccmc_set_state")
