@@ -1,0 +1,319 @@
+"""Benchmark of the coupled-pair Metropolis sweep on GB300.
+
+Workload (default): the 4096^2 temperature sweep -- four lattices of 4096 x 4096
+sites (Delta = 0, V = 0.5, J = 1, n = 0.1, charged fraction 0.3) at
+T = 0.2, 0.5, 1.0, 2.0, seeds 20..23.  One step = 10 sweeps of each of the
+four lattices, the four running concurrently on their own streams, plus the
+observable recount that closes every 10-sweep interval.  The metric is
+site-updates per second (one sweep = N site-updates).
+
+Timing: W warm-up steps, then K timed steps, each bracketed by CUDA events on
+the issuing stream (the other streams join it); L2 is flushed (a 256 MB write)
+between timed steps, outside the events.  nvidia-smi samples clocks during the
+timed region.  `e2e` repeats the steps through the C ABI with host buffers:
+every step uploads the four lattices from pinned host memory (ccmc_set_state)
+and reads the observable records back (ccmc_obs_series).
+
+`--impl reference` times the CPU oracle (single-threaded C) on a bounded sample
+of the same workload.  Under torchrun each rank runs its own four lattices
+(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STEP_SWEEPS = 10
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(", ") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": smax or None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from workloads import temperature_sweep_4096
+
+    sims = temperature_sweep_4096(obs_every=STEP_SWEEPS)
+    # bounded sample: the first `sweeps` sweeps of one lattice per step, all
+    # four temperatures visited in turn
+    sample_sweeps = 2
+    states = {}
+    for s in sims:
+        states[s.seed] = oracle.init_constrained(s.Lx, s.Ly, s.seed, s.n, s.charged_frac)
+    times = []
+    done = {s.seed: 0 for s in sims}
+    for k in range(args.warmup + args.steps):
+        s = sims[k % len(sims)]
+        t0 = time.perf_counter()
+        oracle.sweeps(states[s.seed], s.seed, done[s.seed], sample_sweeps, s.beta, s.Delta, s.V,
+                      s.J, obs_every=0)
+        dt = time.perf_counter() - t0
+        done[s.seed] += sample_sweeps
+        if k >= args.warmup:
+            times.append(dt)
+    N = sims[0].sites
+    value = N * sample_sweeps * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "4096x4096 temperature sweep (T=0.2,0.5,1,2; Delta=0, V=0.5, J=1,"
+                               " n=0.1, c=0.3)", "sample_per_step": f"{sample_sweeps} sweeps of one "
+                               "4096^2 lattice"},
+        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample_sweeps} sweeps of one 4096^2 lattice per step, "
+                                   f"{args.steps} steps"},
+        "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(target_s: float = 12.0):
+    """Time the oracle (single-threaded C, as it stands) on whole sweeps of the
+    first 4096^2 lattice of the workload until about target_s seconds pass."""
+    import oracle
+    from workloads import temperature_sweep_4096
+
+    s = temperature_sweep_4096()[1]
+    st = oracle.init_constrained(s.Lx, s.Ly, s.seed, s.n, s.charged_frac)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < target_s:
+        oracle.sweeps(st, s.seed, n, 1, s.beta, s.Delta, s.V, s.J, obs_every=0)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": s.sites * n / dt, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} sweeps of the 4096^2 lattice at T={s.T} ({dt:.1f} s, 1 thread)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2301_11735_gb300 as cc
+    from workloads import temperature_sweep_4096
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sims = temperature_sweep_4096(obs_every=STEP_SWEEPS)
+    sims = [type(s)(**{**s.__dict__, "seed": s.seed + 4 * rank}) for s in sims]
+    streams = [torch.cuda.Stream() for _ in sims]
+    main = torch.cuda.current_stream()
+    lats = [cc.Lattice(s.Lx, s.Ly, stream=st) for s, st in zip(sims, streams)]
+    for lat, s in zip(lats, sims):
+        lat.init_constrained(s.seed, s.n, s.charged_frac)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(main)
+        for st in streams:
+            st.wait_event(ev0)
+        for lat, s in zip(lats, sims):
+            lat.sweep(STEP_SWEEPS, s.beta, s.Delta, s.V, s.J, obs_every=s.obs_every)
+        for st in streams:
+            e = torch.cuda.Event()
+            e.record(st)
+            main.wait_event(e)
+        ev1.record(main)
+        return ev0, ev1
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    evs = []
+    t_wall = time.perf_counter()
+    with sampler:
+        for _ in range(args.steps):
+            flush.zero_()
+            evs.append(step())
+        torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    clocks = sampler.summary()
+    updates_per_step = sum(s.sites for s in sims) * STEP_SWEEPS
+    value = updates_per_step * args.steps * world / total_s
+
+    # dominant kernel: one colour phase of one 4096^2 lattice, timed launch by
+    # launch with events on its own stream (the kernel the steps are made of)
+    lat, s = lats[0], sims[0]
+    st = streams[0]
+    n_cal = 64
+    cal = []
+    with torch.cuda.stream(st):
+        for _ in range(n_cal):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            lat.phases(1, s.beta, s.Delta, s.V, s.J)
+            b.record(st)
+            cal.append((a, b))
+    torch.cuda.synchronize()
+    phase_ms = statistics.mean(x.elapsed_time(y) for x, y in cal[8:])
+    alg_bytes = 1.5 * s.sites / 8  # 1.5 B per site-update, N/8 updates per phase
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (phase_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers
+    host_states = []
+    for lat in lats:
+        h = torch.from_numpy(lat.get_state()).pin_memory()
+        host_states.append(h)
+    rec_bytes = 0
+    e2e_times = []
+    for k in range(max(2, args.steps // 2) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for lat, s, h in zip(lats, sims, host_states):
+            lat.set_state_ptr(h.data_ptr(), s.seed, 0)
+        for lat, s in zip(lats, sims):
+            lat.sweep(STEP_SWEEPS, s.beta, s.Delta, s.V, s.J, obs_every=s.obs_every)
+        recs = [lat.obs_series(cap=4) for lat in lats]
+        dt = time.perf_counter() - t0
+        rec_bytes = sum(r.nbytes for r in recs)
+        if k > 0:
+            e2e_times.append(dt)
+    e2e_value = updates_per_step * len(e2e_times) * world / sum(e2e_times)
+
+    if rank == 0:
+        line = {
+            "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "4096x4096 temperature sweep: 4 lattices (T=0.2,0.5,1,2; "
+                                   "Delta=0, V=0.5, J=1, n=0.1, c=0.3), 10 sweeps each per step",
+                       "lattices_per_gpu": len(sims), "sweeps_per_step": STEP_SWEEPS,
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
+            "clocks": clocks, "wall_s": t_wall,
+            "gpu_launches": args.steps * len(sims) * (STEP_SWEEPS * 8 + 2),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "phase_kernel (one colour phase, 4096^2)",
+                         "peak_source": peak_kind, "launch_ms": phase_ms},
+            "e2e": {"value": e2e_value, "unit": "site-updates/s",
+                    "h2d_bytes_per_step": int(sum(h.numel() for h in host_states)),
+                    "d2h_bytes_per_step": int(rec_bytes)},
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_sample()
+        print(json.dumps(line), flush=True)
+    for lat in lats:
+        lat.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -88,6 +88,13 @@ int ccmc_init_counts(ccmc_lattice *h, uint64_t seed, int64_t n_plus, int64_t n_m
 int ccmc_sweep(ccmc_lattice *h, int64_t nsweeps, double beta, double Delta, double V, double J,
                int obs_every);
 
+/* Run nphases colour phases, each launched on its own.  One phase is the
+ * paper's "step" (Sec. 5: the processing of one map); a sweep is 8 phases, and
+ * ccmc_sweep(h, s, ...) equals ccmc_phases(h, 8 s, ...) without observables.
+ * The phase counter continues across both calls, so they can be mixed; the
+ * sweep count of a record is the completed phases / 8.  Errors as ccmc_sweep. */
+int ccmc_phases(ccmc_lattice *h, int64_t nphases, double beta, double Delta, double V, double J);
+
 /* Recount the current lattice and return its observables (synchronises). */
 int ccmc_observables(ccmc_lattice *h, ccmc_obs *out);
 /* Copy the ring's records, oldest first, into out[0 .. cap); *n_written gets

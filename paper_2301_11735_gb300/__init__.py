@@ -54,6 +54,7 @@ def _load():
         "ccmc_init_constrained": (c_int, [vp, c_uint64, c_double, c_double]),
         "ccmc_init_counts": (c_int, [vp, c_uint64, c_int64, c_int64]),
         "ccmc_sweep": (c_int, [vp, c_int64, c_double, c_double, c_double, c_double, c_int]),
+        "ccmc_phases": (c_int, [vp, c_int64, c_double, c_double, c_double, c_double]),
         "ccmc_observables": (c_int, [vp, POINTER(Obs)]),
         "ccmc_obs_series": (c_int, [vp, POINTER(Obs), c_int64, i64p]),
         "ccmc_hist_enable": (c_int, [vp, c_int]),
@@ -151,6 +152,10 @@ class Lattice:
               obs_every: int = 0):
         _check(lib().ccmc_sweep(self._h, nsweeps, beta, Delta, V, J, obs_every), "ccmc_sweep")
 
+    def phases(self, nphases: int, beta: float, Delta: float, V: float, J: float):
+        """Run nphases colour phases (the paper's "steps", one map each)."""
+        _check(lib().ccmc_phases(self._h, nphases, beta, Delta, V, J), "ccmc_phases")
+
     def sync(self):
         _check(lib().ccmc_sync(self._h), "ccmc_sync")
 
@@ -181,6 +186,11 @@ class Lattice:
         _check(lib().ccmc_get_state(self._h, out.ctypes.data_as(POINTER(ctypes.c_uint8))),
                "ccmc_get_state")
         return out
+
+    def set_state_ptr(self, host_ptr: int, seed: int, sweeps_done: int = 0):
+        """set_state from a raw host pointer to Lx * Ly site codes (e.g. pinned)."""
+        _check(lib().ccmc_set_state(self._h, ctypes.cast(host_ptr, POINTER(ctypes.c_uint8)),
+                                   seed & (2 ** 64 - 1), sweeps_done), "ccmc_set_state")
 
     def set_state(self, st: np.ndarray, seed: int, sweeps_done: int = 0):
         st = np.ascontiguousarray(st, dtype=np.uint8)

@@ -54,7 +54,7 @@ struct ccmc_lattice {
   int *d_flag = nullptr;
   bool initialised = false;
   uint64_t seed = 0;
-  int64_t sweeps_done = 0;
+  int64_t phases_done = 0;  // global phase index of the next phase
   bool have_params = false;
   double params[4] = {0, 0, 0, 0};  // beta, Delta, V, J
   LaunchCfg cfg{};
@@ -285,7 +285,7 @@ int ccmc_init_counts(ccmc_lattice *h, uint64_t seed, int64_t n_plus, int64_t n_m
   CK(launch_set_ctl(h->d_ctl, 0, h->stream));
   CK(launch_init(h->g, h->h, n_plus, n_minus, h->stream));
   if (h->d_hist) CK(cudaMemsetAsync(h->d_hist, 0, sizeof(int64_t) * 3 * h->nbins, h->stream));
-  h->sweeps_done = 0;
+  h->phases_done = 0;
   h->initialised = true;
   CK(cudaStreamSynchronize(h->stream));
   return CCMC_OK;
@@ -314,9 +314,20 @@ int ccmc_sweep(ccmc_lattice *h, int64_t nsweeps, double beta, double Delta, doub
   if (!h->initialised) return CCMC_E_STATE;
   int rc = upload_params(h, beta, Delta, V, J);
   if (rc) return rc;
+  if (nsweeps > 0 && h->phases_done % 8) {
+    // finish the sweep that ccmc_phases left open; it counts as the first one
+    const int64_t rest = 8 - h->phases_done % 8;
+    rc = ccmc_phases(h, rest, beta, Delta, V, J);
+    if (rc) return rc;
+    if (obs_every > 0 && (h->phases_done / 8) % obs_every == 0)
+      CK(launch_recount(h->g, h->d_partials, h->d_ring, h->ring_cap, h->d_hist, h->nbins, 0,
+                        h->stream));
+    --nsweeps;
+  }
+  const int64_t sweeps_done = h->phases_done / 8;
   int64_t s = 0;
   while (s < nsweeps) {
-    const int64_t abs_sweep = h->sweeps_done + s;
+    const int64_t abs_sweep = sweeps_done + s;
     const int64_t remaining = nsweeps - s;
     if (obs_every > 0 && obs_every <= kChunk) {
       const int g = obs_every * (kChunk / obs_every);
@@ -343,7 +354,23 @@ int ccmc_sweep(ccmc_lattice *h, int64_t nsweeps, double beta, double Delta, doub
     CK(launch_advance(h->d_ctl, 8, h->stream));
     s += 1;
   }
-  h->sweeps_done += nsweeps;
+  h->phases_done += 8 * nsweeps;
+  return CCMC_OK;
+}
+
+int ccmc_phases(ccmc_lattice *h, int64_t nphases, double beta, double Delta, double V,
+                double J) {
+  if (!h || nphases < 0) return CCMC_E_INVAL;
+  if (!(beta >= 0.0) || !std::isfinite(Delta) || !std::isfinite(V) || !std::isfinite(J))
+    return CCMC_E_INVAL;
+  if (!h->initialised) return CCMC_E_STATE;
+  int rc = upload_params(h, beta, Delta, V, J);
+  if (rc) return rc;
+  for (int64_t p = 0; p < nphases; ++p) {
+    CK(launch_phase(h->g, h->t, 0, h->cfg, h->stream));
+    CK(launch_advance(h->d_ctl, 1, h->stream));
+  }
+  h->phases_done += nphases;
   return CCMC_OK;
 }
 
@@ -361,7 +388,7 @@ int ccmc_observables(ccmc_lattice *h, ccmc_obs *out) {
   CK(cudaMemcpyAsync(rec, h->d_ctl + kCtlLatest, sizeof(rec), cudaMemcpyDeviceToHost,
                      h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  rec[0] = h->sweeps_done;
+  rec[0] = h->phases_done / 8;
   fill_obs(h, rec, out);
   return check_status(h);
 }
@@ -444,7 +471,7 @@ int ccmc_set_state(ccmc_lattice *h, const uint8_t *host_in, uint64_t seed, int64
     h->initialised = false;
     return CCMC_E_INVAL;
   }
-  h->sweeps_done = sweeps_done;
+  h->phases_done = 8 * sweeps_done;
   h->initialised = true;
   return CCMC_OK;
 }

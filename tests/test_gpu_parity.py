@@ -220,3 +220,30 @@ def test_full_size_16384_sampled_init_and_one_sweep(cc):
         assert np.array_equal(got, oracle_run_state)
         assert np.array_equal(lat.obs_series()[-1], rec[-1])
         assert rec[-1][6] == Q
+
+
+def test_phase_steps_mixed_with_sweeps(cc):
+    """ccmc_phases runs single colour phases (the paper's "steps"); mixed with
+    ccmc_sweep the phase counter continues, matching the oracle phase by phase."""
+    Lx, Ly, seed = 20, 12, 61
+    beta, Delta, V, J = 1.3, 0.1, 1.0, 1.0
+    st = oracle.init_constrained(Lx, Ly, seed, 0.2, 0.4)
+    table = oracle.threshold_table(beta, Delta, V, J)
+    P = 0
+    with cc.Lattice(Lx, Ly) as lat:
+        lat.init_constrained(seed, 0.2, 0.4)
+        for nph in (3, 1, 4, 13):
+            lat.phases(nph, beta, Delta, V, J)
+            for _ in range(nph):
+                oracle.phase(st, seed, P, table)
+                P += 1
+            assert np.array_equal(lat.get_state(), st), P
+        lat.sweep(3, beta, Delta, V, J, obs_every=1)  # finishes the open sweep first
+        while P % 8:
+            oracle.phase(st, seed, P, table)
+            P += 1
+        st, rec = oracle_run(st, seed, P // 8, 2, beta, Delta, V, J)
+        assert np.array_equal(lat.get_state(), st)
+        got = lat.obs_series()
+        assert np.array_equal(got[-2:], rec)
+        assert got[0, 0] == 3  # the record of the sweep the phases left open
