@@ -132,34 +132,18 @@ __device__ __forceinline__ Sched draw_schedule(const Geo &g, uint64_t P) {
 }
 
 // ----------------------------------------------------------------------------
-// Pair move (Sec. 3.1).  A pair state is pc = 4 code_a + code_b.
-//   QCLASS: 2 bits per pc: 0 = frozen (q = +-2), 1 = q = +1, 2 = q = 0, 3 = q = -1.
-//   SET_*:  the q-set in the paper's order, one 4-bit pc per entry.
-constexpr uint32_t kQClass = (2u << 0) | (2u << 2) | (1u << 4) | (3u << 6) |  // a = +1/2
-                             (2u << 8) | (2u << 10) | (1u << 12) | (3u << 14) |  // a = -1/2
-                             (1u << 16) | (1u << 18) | (0u << 20) | (2u << 22) |  // a = +1
-                             (3u << 24) | (3u << 26) | (2u << 28) | (0u << 30);   // a = -1
-constexpr uint32_t kSetP = 8u | (9u << 4) | (2u << 8) | (6u << 12);    // q = +1
-constexpr uint32_t kSetM = 12u | (13u << 4) | (3u << 8) | (7u << 12);  // q = -1
-constexpr uint32_t kSet0 = 11u | (14u << 4) | (0u << 8) | (5u << 12) | (1u << 16) | (4u << 20);
-
-// Transition entry for (pc -> npc), built on the host: bits 0-12 base index
-// (dQ class, biases, and for neighbouring pairs the a-b bond term), bits 13-20
-// 41 * dS_a (signed), bits 21-24 dsigma_a, bits 25-28 dsigma_b (signed).  The
-// threshold index is base + (41 dS_a) (SA - SB) + dsig_a GA + dsig_b GB with
-// SA = sum_<a> S + 4, GA = sum_<a> sigma + 4 (and likewise for b).
-__device__ __forceinline__ int trans_index(int32_t e, int sa4, int sb4, int ga4, int gb4) {
-  const uint32_t u = (uint32_t)e;
-  const int base = (int)(u & 0x1FFFu);
-  const int mulS = (int)(u << 11) >> 24;
-  const int dga = (int)(u << 7) >> 28;
-  const int dgb = (int)(u << 3) >> 28;
-  return base + mulS * (sa4 - sb4) + dga * ga4 + dgb * gb4;
+// Byte permute (PTX prmt, generic mode): result byte n is source byte
+// sel[4n..4n+2] of the 8 bytes {a, b}; when sel bit 4n+3 is set the byte is
+// filled with the sign bit of that source byte instead.
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
 }
 
-// Biased neighbour sums of 16 sites held in four neighbour windows, as two
-// words of 4-bit lanes (even sites, odd sites): lane = sum (S + 1) over the
-// four neighbours (in [0, 8]); likewise for sigma.
+// Neighbour sums of 16 sites held in four neighbour windows, in 4-bit lanes:
+// lane u of *_e is site 2u, of *_o site 2u + 1; value = sum over the four
+// neighbours of (S + 1) (s*) or (sigma + 1) (g*), in [0, 8].
 struct Sums {
   uint32_t se, so, ge, go;
 };
@@ -177,8 +161,10 @@ __device__ __forceinline__ void add_neighbour(Sums &s, uint32_t X) {
   s.go += (g1 >> 2) & 0x33333333u;
 }
 
-__device__ __forceinline__ int lane4(uint32_t even, uint32_t odd, int t) {
-  return (int)((((t & 1) ? odd : even) >> (4 * (t >> 1))) & 15u);
+// Byte lanes of group k (sites k, k + 4, k + 8, k + 12) from 4-bit lanes.
+__device__ __forceinline__ uint32_t group_bytes(uint32_t e, uint32_t o, int k) {
+  const uint32_t src = (k & 1) ? o : e;
+  return ((k & 2) ? (src >> 4) : src) & 0x0F0F0F0Fu;
 }
 
 }  // namespace ccmc

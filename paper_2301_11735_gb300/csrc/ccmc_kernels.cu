@@ -67,177 +67,253 @@ __global__ void init_kernel(Geo g, int h, int64_t n_plus, int64_t n_minus) {
 // up to 16 pairs (a, a + r).  It reads the a word, the four neighbour windows
 // of a, the b window and the four neighbour windows of b; evaluates every
 // pair's move; stores the a word and XORs the changed b sites back.
+//
+// Per pair, with pc = 4 code_a + code_b and its 16 random bits (choice byte v,
+// acceptance byte u):
+//   entry  = trans[pc][v mod 12]  -> base, byte coefficients, pc XOR npc
+//   index  = dp4a(coefficients, (D8, GA, GB, 0), base)  (threshold index)
+//   accept = u < thr8[index]; a tie, or v >= 252, is settled exactly by the
+//            slow path with the pair's SLOW random words.
+constexpr int kThr8Words = (kTableN + 3) / 4;
+
 struct PhaseSmem {
-  uint16_t thr[kTableN + 128];  // high halves of the thresholds, 64 entries of slack each side
-  int32_t trans[256];
+  uint2 trans[kTransN];
+  uint32_t thr8[kThr8Words];
   Sched sched;
 };
 
-// Full evaluation of pair t when the fast path cannot decide it: the q = 0
-// choice needs the SLOW stream (v >= 65532), or the 16-bit comparison tied.
-__device__ __noinline__ void pair_slow(const Geo &g, const uint32_t *thr32, const int32_t *trans,
-                                       uint32_t A, uint32_t B, const Sums &sa, const Sums &sb,
-                                       uint32_t group, int t, uint64_t k, uint64_t P,
-                                       uint32_t &dA, uint32_t &dB) {
-  const U4 mv = philox(group, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
-  const int q = t & 3;
-  const uint32_t R = q == 0 ? mv.x : q == 1 ? mv.y : q == 2 ? mv.z : mv.w;
-  const uint32_t ca = (A >> (2 * t)) & 3u, cb = (B >> (2 * t)) & 3u;
-  const uint32_t pc = (ca << 2) | cb;
-  const uint32_t qc = (kQClass >> (2 * pc)) & 3u;
-  if (qc == 0u) return;
-  const U4 sl = philox((uint32_t)k, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, g.k0, g.k1);
-  const uint32_t v = R & 0xFFFFu;
-  uint32_t npc;
-  if (qc == 2u) {
-    uint32_t idx;
-    if (v < 65532u) {
-      idx = v % 6u;
-    } else if (sl.y < 4294967292u) {
-      idx = sl.y % 6u;
-    } else {
-      idx = 0xFFu;  // keep the current configuration
-    }
-    npc = idx == 0xFFu ? pc : (kSet0 >> (4 * idx)) & 15u;
+// Uniform per phase: where the ten windows of a word come from.  Column offsets
+// are in sites, normalised to [0, Cx).
+struct PhaseU {
+  const uint32_t *cA, *cAL, *cAR, *cAU, *cAD, *cB, *cBL, *cBR, *cBU, *cBD;
+  int offAL, offAR, offB, offBL, offBR;
+  int dyAU, dyAD, qy, dyBU, dyBD;
+};
+
+__device__ __forceinline__ int wrap(int v, int n) { return v >= n ? v - n : (v < 0 ? v + n : v); }
+
+__device__ __forceinline__ PhaseU phase_uniform(const Geo &g, const Sched &sc) {
+  PhaseU u;
+  const int ax = sc.a0x, ay = sc.a0y;
+  const int bxx = ax + sc.rx, byy = ay + sc.ry;
+  const int cbx = bxx & 3, cby = byy & 3;
+  auto cls = [&](int cx, int cy) { return g.words + (int64_t)(cy * 4 + cx) * g.cstride; };
+  u.cA = cls(ax, ay);
+  u.cAL = cls((ax + 3) & 3, ay);
+  u.cAR = cls((ax + 1) & 3, ay);
+  u.cAU = cls(ax, (ay + 3) & 3);
+  u.cAD = cls(ax, (ay + 1) & 3);
+  u.cB = cls(cbx, cby);
+  u.cBL = cls((cbx + 3) & 3, cby);
+  u.cBR = cls((cbx + 1) & 3, cby);
+  u.cBU = cls(cbx, (cby + 3) & 3);
+  u.cBD = cls(cbx, (cby + 1) & 3);
+  const int qx = (bxx >> 2) % g.Cx;
+  u.offAL = ax == 0 ? g.Cx - 1 : 0;
+  u.offAR = ax == 3 ? (g.Cx == 1 ? 0 : 1) : 0;
+  u.offB = qx;
+  u.offBL = cbx == 0 ? wrap(qx - 1, g.Cx) : qx;
+  u.offBR = cbx == 3 ? wrap(qx + 1, g.Cx) : qx;
+  u.dyAU = ay == 0 ? -1 : 0;
+  u.dyAD = ay == 3 ? 1 : 0;
+  u.qy = (byy >> 2) % g.Cy;
+  u.dyBU = cby == 0 ? -1 : 0;
+  u.dyBD = cby == 3 ? 1 : 0;
+  return u;
+}
+
+// Window of n sites at column 16 w + off (mod Cx) of one class row.
+template <bool kAligned>
+__device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, int row, int w,
+                                           int off, int n) {
+  const uint32_t *r = cls + row * g.W;
+  if (kAligned) {  // rows are whole words: the window straddles at most two
+    const int wl = wrap(w + (off >> 4), g.W);
+    const int sh = 2 * (off & 15);
+    if (sh == 0) return r[wl];
+    const int wh = wl + 1 == g.W ? 0 : wl + 1;
+    return __funnelshift_r(r[wl], r[wh], sh);
   } else {
-    npc = ((qc == 1u ? kSetP : kSetM) >> (4 * (v & 3u))) & 15u;
-  }
-  if (npc == pc) return;
-  const int idx = trans_index(trans[pc * 16 + npc], lane4(sa.se, sa.so, t),
-                              lane4(sb.se, sb.so, t), lane4(sa.ge, sa.go, t),
-                              lane4(sb.ge, sb.go, t));
-  const uint32_t thr = thr32[min(max(idx, 0), kTableN - 1)];
-  const uint32_t u = (R & 0xFFFF0000u) | (sl.x & 0xFFFFu);
-  if (thr == 0xFFFFFFFFu || u < thr) {
-    const uint32_t x = pc ^ npc;
-    dA |= (x >> 2) << (2 * t);
-    dB |= (x & 3u) << (2 * t);
+    return fetch_window(r, g.W, g.Cx, wrap(16 * w + off, g.Cx), n);
   }
 }
 
-__device__ __forceinline__ void phase_word(const Geo &g, const Sched &sc, const PhaseSmem &sm,
+template <bool kAligned>
+__device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const PhaseSmem &sm,
                                            const uint32_t *thr32, int j, int w, uint64_t P) {
   const int s0 = w << 4;
-  const int n = min(16, g.Cx - s0);
-  const int ax = sc.a0x, ay = sc.a0y;
-  const int Cx = g.Cx, Cy = g.Cy, W = g.W;
-  const int jm = j == 0 ? Cy - 1 : j - 1;
-  const int jp = j + 1 == Cy ? 0 : j + 1;
+  const int n = kAligned ? 16 : min(16, g.Cx - s0);
+  const int Cy = g.Cy;
 
-  uint32_t *rowA = row_ptr(g, ay * 4 + ax, j);
+  // ---- gather: the a word, the b window and the eight neighbour windows
+  uint32_t *rowA = const_cast<uint32_t *>(u.cA) + j * g.W;
   const uint32_t A = rowA[w];
-  Sums sa{0u, 0u, 0u, 0u};
-  add_neighbour(sa, fetch_window(row_ptr(g, ay * 4 + ((ax + 3) & 3), j), W, Cx,
-                                 ax == 0 ? (s0 == 0 ? Cx - 1 : s0 - 1) : s0, n));
-  add_neighbour(sa, fetch_window(row_ptr(g, ay * 4 + ((ax + 1) & 3), j), W, Cx,
-                                 ax == 3 ? (s0 + 1 == Cx ? 0 : s0 + 1) : s0, n));
-  add_neighbour(sa, row_ptr(g, ((ay + 3) & 3) * 4 + ax, ay == 0 ? jm : j)[w]);
-  add_neighbour(sa, row_ptr(g, ((ay + 1) & 3) * 4 + ax, ay == 3 ? jp : j)[w]);
+  Sums sa{0u, 0u, 0u, 0u}, sb{0u, 0u, 0u, 0u};
+  add_neighbour(sa, window<kAligned>(u.cAL, g, j, w, u.offAL, n));
+  add_neighbour(sa, window<kAligned>(u.cAR, g, j, w, u.offAR, n));
+  add_neighbour(sa, u.cAU[wrap(j + u.dyAU, Cy) * g.W + w]);
+  add_neighbour(sa, u.cAD[wrap(j + u.dyAD, Cy) * g.W + w]);
+  const int jb = wrap(j + u.qy, Cy);
+  const uint32_t B = window<kAligned>(u.cB, g, jb, w, u.offB, n);
+  add_neighbour(sb, window<kAligned>(u.cBL, g, jb, w, u.offBL, n));
+  add_neighbour(sb, window<kAligned>(u.cBR, g, jb, w, u.offBR, n));
+  add_neighbour(sb, window<kAligned>(u.cBU, g, wrap(jb + u.dyBU, Cy), w, u.offB, n));
+  add_neighbour(sb, window<kAligned>(u.cBD, g, wrap(jb + u.dyBD, Cy), w, u.offB, n));
 
-  const int bxx = ax + sc.rx, byy = ay + sc.ry;
-  const int cbx = bxx & 3, cby = byy & 3;
-  int jb = j + (byy >> 2);
-  if (jb >= Cy) jb -= Cy;
-  int sbb = s0 + (bxx >> 2);
-  if (sbb >= Cx) sbb -= Cx;
-  const int jbm = jb == 0 ? Cy - 1 : jb - 1;
-  const int jbp = jb + 1 == Cy ? 0 : jb + 1;
-  uint32_t *rowB = row_ptr(g, cby * 4 + cbx, jb);
-  const uint32_t B = fetch_window(rowB, W, Cx, sbb, n);
-  Sums sb{0u, 0u, 0u, 0u};
-  add_neighbour(sb, fetch_window(row_ptr(g, cby * 4 + ((cbx + 3) & 3), jb), W, Cx,
-                                 cbx == 0 ? (sbb == 0 ? Cx - 1 : sbb - 1) : sbb, n));
-  add_neighbour(sb, fetch_window(row_ptr(g, cby * 4 + ((cbx + 1) & 3), jb), W, Cx,
-                                 cbx == 3 ? (sbb + 1 == Cx ? 0 : sbb + 1) : sbb, n));
-  add_neighbour(sb, fetch_window(row_ptr(g, ((cby + 3) & 3) * 4 + cbx, cby == 0 ? jbm : jb), W,
-                                 Cx, sbb, n));
-  add_neighbour(sb, fetch_window(row_ptr(g, ((cby + 1) & 3) * 4 + cbx, cby == 3 ? jbp : jb), W,
-                                 Cx, sbb, n));
-
-  // Random words: pair (i, j) of the class takes word i mod 4 of
-  // Philox(seed, (j Cx4 + i / 4, P_lo, P_hi, MOVE)).
-  uint32_t Rw[16];
-  const uint32_t gbase = (uint32_t)j * (uint32_t)g.Cx4 + (uint32_t)(s0 >> 2);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (4 * q < n) {
-      const U4 r = philox(gbase + q, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
-      Rw[4 * q + 0] = r.x;
-      Rw[4 * q + 1] = r.y;
-      Rw[4 * q + 2] = r.z;
-      Rw[4 * q + 3] = r.w;
+  // ---- random fields: pair (i, j) of the class takes the 16-bit half i mod 2
+  // of word (i mod 8) / 2 of Philox(seed, (j Cx8 + i / 8, P_lo, P_hi, MOVE))
+  const uint32_t gbase = (uint32_t)j * (uint32_t)g.Cx8 + (uint32_t)(2 * w);
+  uint32_t rw[8];
+  {
+    const U4 r0 = philox(gbase, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
+    rw[0] = r0.x;
+    rw[1] = r0.y;
+    rw[2] = r0.z;
+    rw[3] = r0.w;
+    if (!kAligned && n <= 8) {
+      rw[4] = rw[5] = rw[6] = rw[7] = 0u;
     } else {
-      Rw[4 * q + 0] = Rw[4 * q + 1] = Rw[4 * q + 2] = Rw[4 * q + 3] = 0u;
+      const U4 r1 = philox(gbase + 1u, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
+      rw[4] = r1.x;
+      rw[5] = r1.y;
+      rw[6] = r1.z;
+      rw[7] = r1.w;
     }
   }
 
-  uint32_t dA = 0u, dB = 0u, slow = 0u;
+  // ---- pair states in 4-bit lanes: lane u of pcE is site 2u, of pcO site 2u+1
+  const uint32_t pcE = ((A & 0x33333333u) << 2) | (B & 0x33333333u);
+  const uint32_t pcO = (A & 0xCCCCCCCCu) | ((B >> 2) & 0x33333333u);
+
+  uint32_t dE = 0u, dO = 0u, slow = 0u;
 #pragma unroll
-  for (int t = 0; t < 16; ++t) {
-    if (t < n) {
-      const uint32_t ca = (A >> (2 * t)) & 3u, cb = (B >> (2 * t)) & 3u;
-      const uint32_t pc = (ca << 2) | cb;
-      const uint32_t qc = (kQClass >> (2 * pc)) & 3u;
-      const uint32_t R = Rw[t];
-      const uint32_t v = R & 0xFFFFu;
-      uint32_t npc;
-      if (qc == 2u) {
-        const uint32_t idx = v - 6u * ((v * 43691u) >> 18);  // v mod 6 for v < 2^16
-        npc = (kSet0 >> (4 * idx)) & 15u;
-        if (v >= 65532u) slow |= 1u << t;
-      } else {
-        npc = ((qc == 1u ? kSetP : kSetM) >> (4 * (v & 3u))) & 15u;
-      }
-      if (qc != 0u && npc != pc && !((slow >> t) & 1u)) {
-        const int idx = trans_index(sm.trans[pc * 16 + npc], lane4(sa.se, sa.so, t),
-                                    lane4(sb.se, sb.so, t), lane4(sa.ge, sa.go, t),
-                                    lane4(sb.ge, sb.go, t));
-        const uint32_t th = sm.thr[64 + idx];
-        const uint32_t uhi = R >> 16;
-        if (uhi < th) {
-          const uint32_t x = pc ^ npc;
-          dA |= (x >> 2) << (2 * t);
-          dB |= (x & 3u) << (2 * t);
-        } else if (uhi == th) {
-          slow |= 1u << t;
-        }
+  for (int k = 0; k < 4; ++k) {
+    // byte lanes of group k (sites k, k+4, k+8, k+12): D8 = SA - SB + 8, GA, GB
+    const uint32_t d8 = group_bytes(sa.se, sa.so, k) + 0x08080808u - group_bytes(sb.se, sb.so, k);
+    const uint32_t ga = group_bytes(sa.ge, sa.go, k);
+    const uint32_t gb = group_bytes(sb.ge, sb.go, k);
+    const uint32_t x01 = prmt(d8, ga, 0x5140u), x23 = prmt(d8, ga, 0x7362u);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int t = 4 * b + k;
+      if (!kAligned && t >= n) continue;
+      const uint32_t env = b == 0 ? prmt(x01, gb, 0x8410u) : b == 1 ? prmt(x01, gb, 0x8532u)
+                         : b == 2 ? prmt(x23, gb, 0x8610u) : prmt(x23, gb, 0x8732u);
+      const uint32_t pc = (((t & 1) ? pcO : pcE) >> (4 * (t >> 1))) & 15u;
+      const uint32_t r16 = rw[t >> 1] >> (16 * (t & 1));
+      const uint32_t v = r16 & 0xFFu, uh = (r16 >> 8) & 0xFFu;
+      const uint32_t r12 = v - 12u * ((v * 171u) >> 11);  // v mod 12 for v < 256
+      const uint2 e = sm.trans[pc * 12u + r12];
+      const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
+      const uint32_t th = (sm.thr8[idx >> 2] >> (8 * (idx & 3))) & 0xFFu;
+      if (v >= 252u || uh == th) {
+        slow |= 1u << t;
+      } else if (uh < th) {
+        const uint32_t x = e.y >> 24;
+        if (t & 1)
+          dO |= x << (4 * (t >> 1));
+        else
+          dE |= x << (4 * (t >> 1));
       }
     }
   }
+  uint32_t dA = ((dE >> 2) & 0x33333333u) | (((dO >> 2) & 0x33333333u) << 2);
+  uint32_t dB = (dE & 0x33333333u) | ((dO & 0x33333333u) << 2);
+
+  // ---- exact path for the undecided pairs (about one in a few hundred)
   while (slow) {
     const int t = __ffs(slow) - 1;
     slow &= slow - 1u;
-    pair_slow(g, thr32, sm.trans, A, B, sa, sb, gbase + (uint32_t)(t >> 2), t,
-              (uint64_t)j * Cx + s0 + t, P, dA, dB);
+    const uint32_t pc = (((A >> (2 * t)) & 3u) << 2) | ((B >> (2 * t)) & 3u);
+    const U4 mv = philox(gbase + (uint32_t)(t >> 3), (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE,
+                         g.k0, g.k1);
+    const int qw = (t & 7) >> 1;
+    const uint32_t word = qw == 0 ? mv.x : qw == 1 ? mv.y : qw == 2 ? mv.z : mv.w;
+    const uint32_t r16 = word >> (16 * (t & 1));
+    const uint32_t v = r16 & 0xFFu, uh = (r16 >> 8) & 0xFFu;
+    const uint64_t kk = (uint64_t)j * g.Cx + s0 + t;
+    const U4 sl = philox((uint32_t)kk, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, g.k0, g.k1);
+    uint32_t r;
+    if (v < 252u)
+      r = v % 12u;
+    else if (sl.y < 4294967292u)
+      r = sl.y % 12u;
+    else
+      continue;  // keep the current configuration
+    const uint2 e = sm.trans[pc * 12u + r];
+    const int sh = 4 * (t >> 1);
+    const uint32_t sa4 = (((t & 1) ? sa.so : sa.se) >> sh) & 15u;
+    const uint32_t sb4 = (((t & 1) ? sb.so : sb.se) >> sh) & 15u;
+    const uint32_t ga4 = (((t & 1) ? sa.go : sa.ge) >> sh) & 15u;
+    const uint32_t gb4 = (((t & 1) ? sb.go : sb.ge) >> sh) & 15u;
+    const uint32_t env = (sa4 + 8u - sb4) | (ga4 << 8) | (gb4 << 16);
+    const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
+    const uint32_t thr = thr32[idx];
+    const uint32_t uu = (uh << 24) | (sl.x & 0xFFFFFFu);
+    if (thr == 0xFFFFFFFFu || uu < thr) {
+      const uint32_t x = e.y >> 24;
+      dA |= (x >> 2) << (2 * t);
+      dB |= (x & 3u) << (2 * t);
+    }
   }
+  if constexpr (!kAligned) {
+    if (n < 16) {
+      const uint32_t valid = (1u << (2 * n)) - 1u;
+      dA &= valid;
+      dB &= valid;
+    }
+  }
+
+  // ---- write back: the a word is this thread's alone; the b sites share words
   if (dA) rowA[w] = A ^ dA;
-  scatter_xor(rowB, Cx, sbb, n, dB);
+  if (dB) {
+    uint32_t *rb = const_cast<uint32_t *>(u.cB) + jb * g.W;
+    if (kAligned) {
+      const int wl = wrap(w + (u.offB >> 4), g.W);
+      const int sh = 2 * (u.offB & 15);
+      atomicXor(rb + wl, dB << sh);
+      if (sh) {
+        const uint32_t hi = dB >> (32 - sh);
+        if (hi) atomicXor(rb + (wl + 1 == g.W ? 0 : wl + 1), hi);
+      }
+    } else {
+      scatter_xor(rb, g.Cx, wrap(s0 + u.offB, g.Cx), n, dB);
+    }
+  }
 }
 
-__global__ void __launch_bounds__(256) phase_kernel(Geo g, const uint16_t *thr16,
+template <bool kAligned>
+__global__ void __launch_bounds__(256) phase_kernel(Geo g, const uint32_t *thr8,
                                                     const uint32_t *thr32,
-                                                    const int32_t *trans_far,
-                                                    const int32_t *trans_near, int64_t p_off) {
+                                                    const uint32_t *trans_far,
+                                                    const uint32_t *trans_near, int64_t p_off) {
   __shared__ PhaseSmem sm;
   const uint64_t P = (uint64_t)(g.ctl[kCtlPhaseBase] + p_off);
   if (threadIdx.x < 32) {
     const Sched s = draw_schedule(g, P);
     if (threadIdx.x == 0) sm.sched = s;
   }
-  for (int t = threadIdx.x; t < kTableN + 128; t += blockDim.x) {
-    const int src = t - 64;
-    sm.thr[t] = (src >= 0 && src < kTableN) ? thr16[src] : (uint16_t)0;
-  }
+  for (int t = threadIdx.x; t < kThr8Words; t += blockDim.x) sm.thr8[t] = thr8[t];
   __syncthreads();
   const Sched sc = sm.sched;
-  const int32_t *trans = sc.near ? trans_near : trans_far;
-  for (int t = threadIdx.x; t < 256; t += blockDim.x) sm.trans[t] = trans[t];
+  const uint32_t *trans = sc.near ? trans_near : trans_far;
+  for (int t = threadIdx.x; t < kTransN; t += blockDim.x)
+    sm.trans[t] = make_uint2(trans[2 * t], trans[2 * t + 1]);
   __syncthreads();
-  const int64_t nw = (int64_t)g.Cy * g.W;
-  for (int64_t wid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; wid < nw;
-       wid += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(wid / g.W), w = (int)(wid - (int64_t)j * g.W);
-    phase_word(g, sc, sm, thr32, j, w, P);
+  const PhaseU u = phase_uniform(g, sc);
+  const int nw = g.Cy * g.W;
+  int wid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  int j = wid / g.W, w = wid - j * g.W;
+  const int sj = stride / g.W, sw = stride - sj * g.W;
+  for (; wid < nw; wid += stride) {
+    phase_word<kAligned>(g, u, sm, thr32, j, w, P);
+    w += sw;
+    j += sj;
+    if (w >= g.W) {
+      w -= g.W;
+      ++j;
+    }
   }
 }
 
@@ -425,8 +501,12 @@ cudaError_t launch_init(const Geo &g, int h, int64_t n_plus, int64_t n_minus, cu
 cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const LaunchCfg &cfg,
                          cudaStream_t s) {
   const int64_t nw = (int64_t)g.Cy * g.W;
-  phase_kernel<<<grid_for(nw, 256, cfg.phase_grid_cap), 256, 0, s>>>(
-      g, t.thr16, t.thr32, t.trans_far, t.trans_near, p_off);
+  const int grid = grid_for(nw, 256, cfg.phase_grid_cap);
+  const uint32_t *thr8 = reinterpret_cast<const uint32_t *>(t.thr8);
+  if ((g.Cx & 15) == 0)
+    phase_kernel<true><<<grid, 256, 0, s>>>(g, thr8, t.thr32, t.trans_far, t.trans_near, p_off);
+  else
+    phase_kernel<false><<<grid, 256, 0, s>>>(g, thr8, t.thr32, t.trans_far, t.trans_near, p_off);
   return cudaGetLastError();
 }
 

@@ -39,37 +39,68 @@ void build_thresholds(double beta, double Delta, double V, double J, uint32_t *t
             threshold(beta, Delta, V, J, 2 * dqi - 2, dBV, dBJ);
 }
 
-// Transition entries for pc = 4 a + b -> npc (see trans_index in the device
-// header).  dE of a pair move (Sec. 3.1):
+// Move entries (see the phase kernel).  For pair state pc = 4 a + b and choice
+// class r = v mod 12, the proposed state is the (r mod |set|)-th configuration
+// of the pair's q-set in the paper's order (Sec. 3.1); frozen pairs (|q| = 2)
+// propose themselves.  dE of the move:
 //   dBV = dS_a sum_<a> S + dS_b sum_<b> S + m dS_a dS_b
 //   dBJ = dsig_a sum_<a> sigma + dsig_b sum_<b> sigma + m dsig_a dsig_b
 // with neighbour sums over old states (partner included) and m the number of
-// a-b bonds (0 or 1 here).  Because dS_b = -dS_a the V term is
-// dS_a (SA - SB) in the biased sums SA = sum S + 4; the sigma biases and the
-// m-term are folded into the base index.
-void build_transitions(int32_t *trans_far, int32_t *trans_near) {
+// a-b bonds.  As dS_b = -dS_a, the threshold index
+//   ((dQ + 2)/2 * 41 + dBV + 20) * 41 + dBJ + 20
+// is an affine function of the biased sums D8 = sum_<a> S - sum_<b> S + 8,
+// GA = sum_<a> sigma + 4, GB = sum_<b> sigma + 4:
+//   index = base + (41 dS_a) D8 + dsig_a GA + dsig_b GB.
+// Entry word 0 holds base; word 1 holds the signed byte coefficients
+// (41 dS_a, dsig_a, dsig_b) and, in its top byte, pc XOR npc.
+namespace {
+constexpr int kSetN[3] = {4, 6, 4};  // q = +1, 0, -1
+constexpr int kSets[3][6][2] = {
+    {{2, 0}, {2, 1}, {0, 2}, {1, 2}, {0, 0}, {0, 0}},  // q = +1
+    {{2, 3}, {3, 2}, {0, 0}, {1, 1}, {0, 1}, {1, 0}},  // q = 0
+    {{3, 0}, {3, 1}, {0, 3}, {1, 3}, {0, 0}, {0, 0}},  // q = -1
+};
+}  // namespace
+
+bool build_transitions(uint32_t *trans_far, uint32_t *trans_near) {
+  int lo = 1 << 30, hi = -(1 << 30);
   for (int pc = 0; pc < 16; ++pc) {
-    for (int npc = 0; npc < 16; ++npc) {
-      const int ca = pc >> 2, cb = pc & 3, na = npc >> 2, nb = npc & 3;
-      const int q0 = kS[ca] + kS[cb], q1 = kS[na] + kS[nb];
-      int32_t far = 0, nearv = 0;
-      if (q0 == q1 && q0 >= -1 && q0 <= 1) {
-        const int dQ = kS[na] * kS[na] + kS[nb] * kS[nb] - kS[ca] * kS[ca] - kS[cb] * kS[cb];
-        const int dSa = kS[na] - kS[ca], dSb = kS[nb] - kS[cb];
-        const int dGa = kSigma[na] - kSigma[ca], dGb = kSigma[nb] - kSigma[cb];
-        const int dqi = (dQ + 2) / 2;
-        const int base = dqi * kNB * kNB + kDB * kNB + kDB - 4 * (dGa + dGb);
-        const int near_base = base + kNB * dSa * dSb + dGa * dGb;
-        const uint32_t fields = ((static_cast<uint32_t>(kNB * dSa) & 0xFFu) << 13) |
-                                ((static_cast<uint32_t>(dGa) & 0xFu) << 21) |
-                                ((static_cast<uint32_t>(dGb) & 0xFu) << 25);
-        far = static_cast<int32_t>((static_cast<uint32_t>(base) & 0x1FFFu) | fields);
-        nearv = static_cast<int32_t>((static_cast<uint32_t>(near_base) & 0x1FFFu) | fields);
+    const int ca = pc >> 2, cb = pc & 3;
+    const int q = kS[ca] + kS[cb];
+    for (int r = 0; r < 12; ++r) {
+      int na = ca, nb = cb;
+      if (q >= -1 && q <= 1) {
+        const int qi = 1 - q;
+        na = kSets[qi][r % kSetN[qi]][0];
+        nb = kSets[qi][r % kSetN[qi]][1];
       }
-      trans_far[pc * 16 + npc] = far;
-      trans_near[pc * 16 + npc] = nearv;
+      const int dQ = kS[na] * kS[na] + kS[nb] * kS[nb] - kS[ca] * kS[ca] - kS[cb] * kS[cb];
+      const int dSa = kS[na] - kS[ca], dSb = kS[nb] - kS[cb];
+      const int dGa = kSigma[na] - kSigma[ca], dGb = kSigma[nb] - kSigma[cb];
+      const int mulS = kNB * dSa;
+      const int base = (dQ + 2) / 2 * kNB * kNB + kDB * kNB + kDB - 4 * (dGa + dGb) - 8 * mulS;
+      const int near_base = base + kNB * dSa * dSb + dGa * dGb;
+      const uint32_t x = (uint32_t)(((ca ^ na) << 2) | (cb ^ nb));
+      const uint32_t coef = ((uint32_t)mulS & 0xFFu) | (((uint32_t)dGa & 0xFFu) << 8) |
+                            (((uint32_t)dGb & 0xFFu) << 16) | (x << 24);
+      const int e = pc * 12 + r;
+      trans_far[2 * e] = (uint32_t)base;
+      trans_far[2 * e + 1] = coef;
+      trans_near[2 * e] = (uint32_t)near_base;
+      trans_near[2 * e + 1] = coef;
+      // every index an entry can form, over all possible neighbour sums
+      // (D8 in [0, 16], GA and GB in [0, 8]), must stay inside the table
+      for (int b0 : {base, near_base})
+        for (int D8 : {0, 16})
+          for (int ga : {0, 8})
+            for (int gb : {0, 8}) {
+              const int idx = b0 + mulS * D8 + dGa * ga + dGb * gb;
+              lo = idx < lo ? idx : lo;
+              hi = idx > hi ? idx : hi;
+            }
     }
   }
+  return lo >= 0 && hi < kTableN;
 }
 
 }  // namespace ccmc
