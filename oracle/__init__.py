@@ -142,13 +142,13 @@ def pair_delta(st: np.ndarray, a: int, b: int, na: int, nb: int):
     return tuple(out)
 
 
-def pair_move(st: np.ndarray, a: int, b: int, R16: int, key, slow_ctr, table) -> int:
-    """One move; R16 = choice byte | top byte of the acceptance word << 8."""
+def pair_move(st: np.ndarray, a: int, b: int, R: int, key, slow_ctr, table) -> int:
+    """One move; R = 16-bit choice | top half of the acceptance word << 16."""
     Ly, Lx = st.shape
     k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
     c = np.ascontiguousarray(np.asarray(slow_ctr, dtype=np.uint32))
     t = np.ascontiguousarray(table.reshape(-1), dtype=np.uint32)
-    return lib().oracle_pair_move(_u8(st), Lx, Ly, a, b, R16 & 0xFFFF, _p(k, c_uint32),
+    return lib().oracle_pair_move(_u8(st), Lx, Ly, a, b, R & 0xFFFFFFFF, _p(k, c_uint32),
                                   _p(c, c_uint32), _p(t, c_uint32))
 
 

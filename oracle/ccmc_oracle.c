@@ -263,27 +263,27 @@ void oracle_pair_delta(const uint8_t *st, int Lx, int Ly, int a, int b, int na, 
 
 /* One coupled-pair move (Sec. 3.1): q = S_a + S_b; |q| = 2 cannot change;
  * otherwise draw one configuration of the pair's q-set uniformly (the current
- * one included), then apply the Metropolis test to dE.  The pair's random field
- * R16 holds an 8-bit choice v (bits 0-7) and the top byte u_hi of its 32-bit
- * acceptance word (bits 8-15).
- *   choice: v mod |set| when v < 252 (252 is a multiple of 4 and of 6), else
- *           SLOW word 1 mod |set| when it is below 4294967292 (also a multiple
- *           of 12), else the current configuration.
- *   test:   accept iff thr == 0xFFFFFFFF or (u_hi << 24 | u_lo) < thr, with
- *           u_lo the low 24 bits of SLOW word 0. */
-int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t R16,
+ * one included), then apply the Metropolis test to dE.  The pair's 32-bit
+ * random word R holds a 16-bit choice v (bits 0-15) and the top half u_hi of
+ * its 32-bit acceptance word (bits 16-31).
+ *   choice: v mod |set| when v < 65532 (a multiple of 4 and of 6), else SLOW
+ *           word 1 mod |set| when it is below 4294967292 (also a multiple of
+ *           12), else the current configuration.
+ *   test:   accept iff thr == 0xFFFFFFFF or (u_hi << 16 | u_lo) < thr, with
+ *           u_lo the low 16 bits of SLOW word 0. */
+int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t R,
                      const uint32_t key[2], const uint32_t slow_ctr[4], const uint32_t *table) {
   int ca = st[a], cb = st[b];
   int q = CODE_S[ca] + CODE_S[cb];
   if (q == 2 || q == -2) return 0;
-  uint32_t v = R16 & 0xFFu;
-  uint32_t u_hi = (R16 >> 8) & 0xFFu;
+  uint32_t v = R & 0xFFFFu;
+  uint32_t u_hi = R >> 16;
   uint32_t slow[4];
   int have_slow = 0;
   const uint8_t(*set)[2] = (q == 1) ? SET_QP1 : (q == -1) ? SET_QM1 : SET_Q0;
   uint32_t nset = (q == 0) ? 6u : 4u;
   uint32_t idx;
-  if (v < 252u) {
+  if (v < 65532u) {
     idx = v % nset;
   } else {
     oracle_philox4x32_10(slow_ctr, key, slow);
@@ -310,7 +310,7 @@ int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t R16,
       oracle_philox4x32_10(slow_ctr, key, slow);
       have_slow = 1;
     }
-    uint32_t u = (u_hi << 24) | (slow[0] & 0xFFFFFFu);
+    uint32_t u = (u_hi << 16) | (slow[0] & 0xFFFFu);
     accept = u < thr;
   }
   if (!accept) return 0;
@@ -356,10 +356,10 @@ static void write_record(const uint8_t *st, int Lx, int Ly, int64_t sweeps_done,
 
 /* ------------------------------------------------------------------------ */
 /* One colour phase: every pair (a, a + r), a = (4i + a0x, 4j + a0y), with pair
- * index k = j * (Lx/4) + i inside the class.  Pairs come in groups of eight
- * consecutive i of one class row: pair (i, j) takes the 16-bit half i mod 2 of
- * word (i mod 8) / 2 of Philox(seed, (j * ceil(Lx/32) + i/8, P_lo, P_hi, MOVE)),
- * and its slow words from Philox(seed, (k, P_lo, P_hi, SLOW)). */
+ * index k = j * (Lx/4) + i inside the class.  Pairs come in groups of four
+ * consecutive i of one class row: pair (i, j) takes word i mod 4 of
+ * Philox(seed, (j * ceil(Lx/16) + i/4, P_lo, P_hi, MOVE)), and its slow words
+ * from Philox(seed, (k, P_lo, P_hi, SLOW)). */
 void oracle_phase(uint8_t *st, int Lx, int Ly, uint64_t seed, uint64_t P, const uint32_t *table) {
   uint32_t key[2];
   seed_key(seed, key);
@@ -372,13 +372,13 @@ void oracle_phase(uint8_t *st, int Lx, int Ly, uint64_t seed, uint64_t P, const 
       int64_t k = (int64_t)j * Cx + i;
       int ax = 4 * i + a0x, ay = 4 * j + a0y;
       int bx = (ax + rx) % Lx, by = (ay + ry) % Ly;
-      int64_t group = (int64_t)j * ((Cx + 7) / 8) + i / 8;
+      int64_t group = (int64_t)j * ((Cx + 3) / 4) + i / 4;
       uint32_t mctr[4] = {(uint32_t)group, Plo, Phi, ORACLE_TAG_MOVE};
       uint32_t mw[4];
       oracle_philox4x32_10(mctr, key, mw);
-      uint32_t R16 = (mw[(i & 7) >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+      uint32_t R = mw[i & 3];
       uint32_t sctr[4] = {(uint32_t)k, Plo, Phi, ORACLE_TAG_SLOW};
-      oracle_pair_move(st, Lx, Ly, ay * Lx + ax, by * Lx + bx, R16, key, sctr, table);
+      oracle_pair_move(st, Lx, Ly, ay * Lx + ax, by * Lx + bx, R, key, sctr, table);
     }
   }
 }
@@ -405,8 +405,8 @@ int64_t oracle_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0
 /* ------------------------------------------------------------------------ */
 /* Sequential random-pair mode (Sec. 3.1 as a serial algorithm): move t draws an
  * ordered pair index uniform on [0, N(N-1)) from Philox(seed, (t_lo, t_hi,
- * attempt, SEQ)) words 0-1 by multiply-high with rejection; the low half of
- * word 2 is the pair's random field. */
+ * attempt, SEQ)) words 0-1 by multiply-high with rejection; word 2 is the
+ * pair's random word. */
 int64_t oracle_sequential_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
                                  int64_t nsweeps, double beta, double Delta, double V, double J,
                                  int obs_every, int64_t *records) {
@@ -436,7 +436,7 @@ int64_t oracle_sequential_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int
         int b = (int)(pidx % (N - 1));
         if (b >= a) b += 1;
         uint32_t sctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), attempt, ORACLE_TAG_SEQSLOW};
-        oracle_pair_move(st, Lx, Ly, a, b, w[2] & 0xFFFFu, key, sctr, table);
+        oracle_pair_move(st, Lx, Ly, a, b, w[2], key, sctr, table);
         break;
       }
     }

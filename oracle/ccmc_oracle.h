@@ -30,7 +30,7 @@ extern "C" {
 
 /* Counter-space tags (fourth counter word) of the independent random streams. */
 #define ORACLE_TAG_SCHED 1u   /* phase schedule (class a0 and offset r)     */
-#define ORACLE_TAG_MOVE 2u    /* per 8 pairs: 16 bits each, choice | u_hi   */
+#define ORACLE_TAG_MOVE 2u    /* per 4 pairs: one word each, choice | u_hi  */
 #define ORACLE_TAG_SLOW 3u    /* per pair: u_lo and the choice fallback     */
 #define ORACLE_TAG_FEISTEL 4u /* initial-state placement permutation        */
 #define ORACLE_TAG_SIGN 5u    /* initial spin signs of magnetic sites       */
@@ -76,11 +76,11 @@ void oracle_schedule(int Lx, int Ly, uint64_t seed, uint64_t P, int *a0x, int *a
 void oracle_pair_delta(const uint8_t *st, int Lx, int Ly, int a, int b, int na, int nb,
                        int out[3]);
 
-/* One coupled-pair Metropolis move on sites a and b.  R16 is the pair's 16-bit
- * random field (choice byte, then the top byte of the acceptance word); the
+/* One coupled-pair Metropolis move on sites a and b.  R is the pair's 32-bit
+ * random word (16-bit choice, then the top half of the acceptance word); the
  * SLOW words are drawn from Philox(key, slow_ctr) when needed.  Returns 1 if
  * the lattice changed. */
-int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t R16,
+int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t R,
                      const uint32_t key[2], const uint32_t slow_ctr[4], const uint32_t *table);
 
 /* Full recount: out = {Nc, BV, BJ, M, M_stag, S_sum, S_stag}. */

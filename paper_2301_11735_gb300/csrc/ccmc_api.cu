@@ -86,12 +86,12 @@ int upload_params(ccmc_lattice *h, double beta, double Delta, double V, double J
       h->params[3] == J)
     return CCMC_OK;
   std::vector<uint32_t> thr32(kTableN);
-  std::vector<uint8_t> thr8(kThr8Bytes, 0);
+  std::vector<uint16_t> thr16(kThr16Bytes / 2, 0);
   build_thresholds(beta, Delta, V, J, thr32.data());
-  for (int i = 0; i < kTableN; ++i) thr8[i] = (uint8_t)(thr32[i] >> 24);
+  for (int i = 0; i < kTableN; ++i) thr16[i] = (uint16_t)(thr32[i] >> 16);
   CK(cudaMemcpyAsync(h->t.thr32, thr32.data(), sizeof(uint32_t) * kTableN,
                      cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(h->t.thr8, thr8.data(), kThr8Bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->t.thr16, thr16.data(), kThr16Bytes, cudaMemcpyHostToDevice, h->stream));
   // pageable sources: the copies are staged before the calls return
   h->have_params = true;
   h->params[0] = beta;
@@ -206,7 +206,7 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   g.Cx = Lx / 4;
   g.Cy = Ly / 4;
   g.W = (g.Cx + 15) / 16;
-  g.Cx8 = (g.Cx + 7) / 8;
+  g.Cx4 = (g.Cx + 3) / 4;
   g.cstride = (int64_t)g.Cy * g.W;
   const uint64_t N = (uint64_t)Lx * (uint64_t)Ly;
   g.rej = (0 - N) % N;
@@ -231,7 +231,7 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
       cudaMalloc(&h->d_ring, sizeof(int64_t) * 8 * h->ring_cap) != cudaSuccess ||
       cudaMalloc(&h->d_flag, sizeof(int)) != cudaSuccess)
     return fail(CCMC_E_NOMEM);
-  const size_t tb = sizeof(uint32_t) * kTableN + 2 * sizeof(uint32_t) * 2 * kTransN + kThr8Bytes;
+  const size_t tb = sizeof(uint32_t) * kTableN + 2 * sizeof(uint32_t) * 2 * kTransN + kThr16Bytes;
   if (cudaMalloc(&h->d_tables, tb) != cudaSuccess) return fail(CCMC_E_NOMEM);
   char *p = (char *)h->d_tables;
   h->t.thr32 = (uint32_t *)p;
@@ -240,7 +240,7 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   p += sizeof(uint32_t) * 2 * kTransN;
   h->t.trans_near = (uint32_t *)p;
   p += sizeof(uint32_t) * 2 * kTransN;
-  h->t.thr8 = (uint8_t *)p;
+  h->t.thr16 = (uint16_t *)p;
   g.words = h->d_words;
   g.ctl = h->d_ctl;
   uint32_t tf[2 * kTransN], tn[2 * kTransN];

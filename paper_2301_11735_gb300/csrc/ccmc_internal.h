@@ -9,7 +9,7 @@
 namespace ccmc {
 
 constexpr uint32_t TAG_SCHED = 1u;    // phase schedule
-constexpr uint32_t TAG_MOVE = 2u;     // per 8-pair group: 16 bits a pair
+constexpr uint32_t TAG_MOVE = 2u;     // per 4-pair group: one word a pair
 constexpr uint32_t TAG_SLOW = 3u;     // per pair: u_lo, choice fallback
 constexpr uint32_t TAG_FEISTEL = 4u;  // initial placement
 constexpr uint32_t TAG_SIGN = 5u;     // initial spin signs
@@ -33,7 +33,7 @@ struct Geo {
   uint32_t *words;  // 16 classes x Cy rows x W words
   int64_t *ctl;     // control block
   int Lx, Ly, Cx, Cy, W;
-  int Cx8;          // ceil(Cx / 8): 8-pair random groups per class row
+  int Cx4;          // ceil(Cx / 4): 4-pair random groups per class row
   int64_t cstride;  // Cy * W words per class
   uint32_t k0, k1;  // Philox key = seed
   uint64_t rej;     // 2^64 mod (Lx Ly): Lemire rejection bound
@@ -41,7 +41,7 @@ struct Geo {
 
 // Per-lattice parameter tables in device memory (built on the host).
 struct DevTables {
-  uint8_t *thr8;        // kTableN: top byte of each threshold (fast path)
+  uint16_t *thr16;      // kTableN: top half of each threshold (fast path)
   uint32_t *thr32;      // kTableN: full thresholds (exact path)
   uint32_t *trans_far;  // kTransN x 2 words: move entries, partner not a neighbour
   uint32_t *trans_near; // kTransN x 2 words: move entries, partner a nearest neighbour
@@ -50,7 +50,7 @@ struct DevTables {
 // Move entries are indexed by pair state pc = 4 code_a + code_b and the pair's
 // choice byte mod 12 (12 is a multiple of both q-set sizes, 4 and 6).
 constexpr int kTransN = 16 * 12;
-constexpr int kThr8Bytes = (kTableN + 3) / 4 * 4;
+constexpr int kThr16Bytes = (kTableN + 1) / 2 * 4;
 
 struct LaunchCfg {
   int phase_grid_cap = 152 * 8;

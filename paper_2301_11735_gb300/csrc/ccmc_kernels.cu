@@ -68,17 +68,17 @@ __global__ void init_kernel(Geo g, int h, int64_t n_plus, int64_t n_minus) {
 // of a, the b window and the four neighbour windows of b; evaluates every
 // pair's move; stores the a word and XORs the changed b sites back.
 //
-// Per pair, with pc = 4 code_a + code_b and its 16 random bits (choice byte v,
-// acceptance byte u):
+// Per pair, with pc = 4 code_a + code_b and its 32-bit random word (16-bit
+// choice v, top half u of the acceptance word):
 //   entry  = trans[pc][v mod 12]  -> base, byte coefficients, pc XOR npc
 //   index  = dp4a(coefficients, (D8, GA, GB, 0), base)  (threshold index)
-//   accept = u < thr8[index]; a tie, or v >= 252, is settled exactly by the
-//            slow path with the pair's SLOW random words.
-constexpr int kThr8Words = (kTableN + 3) / 4;
+//   accept = u < thr16[index]; a tie, or v >= 65532, is settled exactly by the
+//            slow path with the pair's SLOW random words (about 1 pair in 10^4).
+constexpr int kThr16Words = (kTableN + 1) / 2;
 
 struct PhaseSmem {
   uint2 trans[kTransN];
-  uint32_t thr8[kThr8Words];
+  uint32_t thr16[kThr16Words];
   Sched sched;
 };
 
@@ -160,53 +160,46 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
   add_neighbour(sb, window<kAligned>(u.cBU, g, wrap(jb + u.dyBU, Cy), w, u.offB, n));
   add_neighbour(sb, window<kAligned>(u.cBD, g, wrap(jb + u.dyBD, Cy), w, u.offB, n));
 
-  // ---- random fields: pair (i, j) of the class takes the 16-bit half i mod 2
-  // of word (i mod 8) / 2 of Philox(seed, (j Cx8 + i / 8, P_lo, P_hi, MOVE))
-  const uint32_t gbase = (uint32_t)j * (uint32_t)g.Cx8 + (uint32_t)(2 * w);
-  uint32_t rw[8];
-  {
-    const U4 r0 = philox(gbase, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
-    rw[0] = r0.x;
-    rw[1] = r0.y;
-    rw[2] = r0.z;
-    rw[3] = r0.w;
-    if (!kAligned && n <= 8) {
-      rw[4] = rw[5] = rw[6] = rw[7] = 0u;
-    } else {
-      const U4 r1 = philox(gbase + 1u, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
-      rw[4] = r1.x;
-      rw[5] = r1.y;
-      rw[6] = r1.z;
-      rw[7] = r1.w;
-    }
-  }
-
   // ---- pair states in 4-bit lanes: lane u of pcE is site 2u, of pcO site 2u+1
   const uint32_t pcE = ((A & 0x33333333u) << 2) | (B & 0x33333333u);
   const uint32_t pcO = (A & 0xCCCCCCCCu) | ((B >> 2) & 0x33333333u);
 
-  uint32_t dE = 0u, dO = 0u, slow = 0u;
+  // ---- byte lanes of group k (sites k, k+4, k+8, k+12): D8 = SA - SB + 8, GA, GB
+  uint32_t x01[4], x23[4], gbk[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    // byte lanes of group k (sites k, k+4, k+8, k+12): D8 = SA - SB + 8, GA, GB
     const uint32_t d8 = group_bytes(sa.se, sa.so, k) + 0x08080808u - group_bytes(sb.se, sb.so, k);
     const uint32_t ga = group_bytes(sa.ge, sa.go, k);
-    const uint32_t gb = group_bytes(sb.ge, sb.go, k);
-    const uint32_t x01 = prmt(d8, ga, 0x5140u), x23 = prmt(d8, ga, 0x7362u);
+    gbk[k] = group_bytes(sb.ge, sb.go, k);
+    x01[k] = prmt(d8, ga, 0x5140u);
+    x23[k] = prmt(d8, ga, 0x7362u);
+  }
+
+  // ---- random words: pair (i, j) of the class takes word i mod 4 of
+  // Philox(seed, (j Cx4 + i / 4, P_lo, P_hi, MOVE)); call b covers pairs 4b..4b+3
+  const uint32_t gbase = (uint32_t)j * (uint32_t)g.Cx4 + (uint32_t)(4 * w);
+  uint32_t dE = 0u, dO = 0u, slow = 0u;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+  for (int b = 0; b < 4; ++b) {
+    if (!kAligned && 4 * b >= n) break;
+    const U4 r = philox(gbase + (uint32_t)b, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0,
+                        g.k1);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
       const int t = 4 * b + k;
       if (!kAligned && t >= n) continue;
-      const uint32_t env = b == 0 ? prmt(x01, gb, 0x8410u) : b == 1 ? prmt(x01, gb, 0x8532u)
-                         : b == 2 ? prmt(x23, gb, 0x8610u) : prmt(x23, gb, 0x8732u);
+      const uint32_t R = k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w;
+      const uint32_t env = b == 0 ? prmt(x01[k], gbk[k], 0x8410u)
+                         : b == 1 ? prmt(x01[k], gbk[k], 0x8532u)
+                         : b == 2 ? prmt(x23[k], gbk[k], 0x8610u)
+                                  : prmt(x23[k], gbk[k], 0x8732u);
       const uint32_t pc = (((t & 1) ? pcO : pcE) >> (4 * (t >> 1))) & 15u;
-      const uint32_t r16 = rw[t >> 1] >> (16 * (t & 1));
-      const uint32_t v = r16 & 0xFFu, uh = (r16 >> 8) & 0xFFu;
-      const uint32_t r12 = v - 12u * ((v * 171u) >> 11);  // v mod 12 for v < 256
+      const uint32_t v = R & 0xFFFFu, uh = R >> 16;
+      const uint32_t r12 = v - 12u * ((v * 43691u) >> 19);  // v mod 12 for v < 2^16
       const uint2 e = sm.trans[pc * 12u + r12];
       const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
-      const uint32_t th = (sm.thr8[idx >> 2] >> (8 * (idx & 3))) & 0xFFu;
-      if (v >= 252u || uh == th) {
+      const uint32_t th = (sm.thr16[idx >> 1] >> (16 * (idx & 1))) & 0xFFFFu;
+      if (v >= 65532u || uh == th) {
         slow |= 1u << t;
       } else if (uh < th) {
         const uint32_t x = e.y >> 24;
@@ -220,21 +213,20 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
   uint32_t dA = ((dE >> 2) & 0x33333333u) | (((dO >> 2) & 0x33333333u) << 2);
   uint32_t dB = (dE & 0x33333333u) | ((dO & 0x33333333u) << 2);
 
-  // ---- exact path for the undecided pairs (about one in a few hundred)
+  // ---- exact path for the undecided pairs
   while (slow) {
     const int t = __ffs(slow) - 1;
     slow &= slow - 1u;
     const uint32_t pc = (((A >> (2 * t)) & 3u) << 2) | ((B >> (2 * t)) & 3u);
-    const U4 mv = philox(gbase + (uint32_t)(t >> 3), (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE,
+    const U4 mv = philox(gbase + (uint32_t)(t >> 2), (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE,
                          g.k0, g.k1);
-    const int qw = (t & 7) >> 1;
-    const uint32_t word = qw == 0 ? mv.x : qw == 1 ? mv.y : qw == 2 ? mv.z : mv.w;
-    const uint32_t r16 = word >> (16 * (t & 1));
-    const uint32_t v = r16 & 0xFFu, uh = (r16 >> 8) & 0xFFu;
+    const int qw = t & 3;
+    const uint32_t R = qw == 0 ? mv.x : qw == 1 ? mv.y : qw == 2 ? mv.z : mv.w;
+    const uint32_t v = R & 0xFFFFu, uh = R >> 16;
     const uint64_t kk = (uint64_t)j * g.Cx + s0 + t;
     const U4 sl = philox((uint32_t)kk, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, g.k0, g.k1);
     uint32_t r;
-    if (v < 252u)
+    if (v < 65532u)
       r = v % 12u;
     else if (sl.y < 4294967292u)
       r = sl.y % 12u;
@@ -249,7 +241,7 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
     const uint32_t env = (sa4 + 8u - sb4) | (ga4 << 8) | (gb4 << 16);
     const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
     const uint32_t thr = thr32[idx];
-    const uint32_t uu = (uh << 24) | (sl.x & 0xFFFFFFu);
+    const uint32_t uu = (uh << 16) | (sl.x & 0xFFFFu);
     if (thr == 0xFFFFFFFFu || uu < thr) {
       const uint32_t x = e.y >> 24;
       dA |= (x >> 2) << (2 * t);
@@ -283,7 +275,7 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
 }
 
 template <bool kAligned>
-__global__ void __launch_bounds__(256) phase_kernel(Geo g, const uint32_t *thr8,
+__global__ void __launch_bounds__(256) phase_kernel(Geo g, const uint32_t *thr16,
                                                     const uint32_t *thr32,
                                                     const uint32_t *trans_far,
                                                     const uint32_t *trans_near, int64_t p_off) {
@@ -293,7 +285,7 @@ __global__ void __launch_bounds__(256) phase_kernel(Geo g, const uint32_t *thr8,
     const Sched s = draw_schedule(g, P);
     if (threadIdx.x == 0) sm.sched = s;
   }
-  for (int t = threadIdx.x; t < kThr8Words; t += blockDim.x) sm.thr8[t] = thr8[t];
+  for (int t = threadIdx.x; t < kThr16Words; t += blockDim.x) sm.thr16[t] = thr16[t];
   __syncthreads();
   const Sched sc = sm.sched;
   const uint32_t *trans = sc.near ? trans_near : trans_far;
@@ -502,11 +494,11 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
                          cudaStream_t s) {
   const int64_t nw = (int64_t)g.Cy * g.W;
   const int grid = grid_for(nw, 256, cfg.phase_grid_cap);
-  const uint32_t *thr8 = reinterpret_cast<const uint32_t *>(t.thr8);
+  const uint32_t *thr16 = reinterpret_cast<const uint32_t *>(t.thr16);
   if ((g.Cx & 15) == 0)
-    phase_kernel<true><<<grid, 256, 0, s>>>(g, thr8, t.thr32, t.trans_far, t.trans_near, p_off);
+    phase_kernel<true><<<grid, 256, 0, s>>>(g, thr16, t.thr32, t.trans_far, t.trans_near, p_off);
   else
-    phase_kernel<false><<<grid, 256, 0, s>>>(g, thr8, t.thr32, t.trans_far, t.trans_near, p_off);
+    phase_kernel<false><<<grid, 256, 0, s>>>(g, thr16, t.thr32, t.trans_far, t.trans_near, p_off);
   return cudaGetLastError();
 }
 

@@ -59,7 +59,7 @@ def test_pair_sets_match_paper_order():
 
 
 def test_q0_choice_fallback_uses_slow_word():
-    # a choice byte >= 252 falls back to SLOW word 1 (mod 6 when below 6 * 715827882)
+    # a choice field >= 65532 falls back to SLOW word 1 (mod 6 when below 6 * 715827882)
     sets = golden_pair_sets()
     table = all_pass_table()
     key = oracle.seed_key(77)
@@ -68,7 +68,7 @@ def test_q0_choice_fallback_uses_slow_word():
         w1 = int(oracle.philox(ctr, key)[1])
         st = np.zeros((4, 4), dtype=np.uint8)
         st.flat[0], st.flat[10] = 0, 0
-        oracle.pair_move(st, 0, 10, 0xFF, key, ctr, table)
+        oracle.pair_move(st, 0, 10, 0xFFFF, key, ctr, table)
         expect = sets[0][w1 % 6] if w1 < 6 * 715827882 else (0, 0)
         assert (st.flat[0], st.flat[10]) == expect
 
