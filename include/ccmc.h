@@ -117,6 +117,26 @@ int ccmc_set_state(ccmc_lattice *h, const uint8_t *host_in, uint64_t seed, int64
 /* Block until the handle's queued work is done; reports a device-side error. */
 int ccmc_sync(ccmc_lattice *h);
 
+/* Observables of a lattice the caller keeps in device memory, computed without
+ * allocating anything -- for callers that cannot let a library allocate device
+ * memory during the call (a server that reserved its whole memory budget up
+ * front, or a latency-critical path that must not pay for cudaMalloc/cudaFree).
+ * The paper has no counterpart; it is a service of this library.
+ *   d_state: Lx * Ly site codes (device memory, site (x, y) at y * Lx + x);
+ *   d_out:   7 int64 in device memory, receives Nc, BV, BJ, M, M_stag, S_sum,
+ *            S_stag exactly as ccmc_observables reports them.
+ * The reduction's scratch is a fixed static device array of 64 KB (1024 block
+ * partials and a counter) that every GPU loading the library holds until exit;
+ * lattices of any size up to Lx * Ly = 2^30 fit it (larger: E_INVAL), and
+ * Lx, Ly >= 2.  The first call on a device looks up that array's address with
+ * the device current; make that first call before any stream capture.  The work
+ * is queued on cuda_stream (NULL: the legacy default stream); synchronise before
+ * reading d_out.  All calls share the one array, so calls that overlap on the
+ * GPU (different streams, or another host thread) race and must not be issued.
+ * Errors: E_INVAL (null pointer or size), E_CUDA. */
+int ccmc_recount_noalloc(const uint8_t *d_state, int Lx, int Ly, int64_t *d_out,
+                         void *cuda_stream);
+
 /* Host-only: the acceptance thresholds the sweep uses (Sec. 3.1, "otherwise
  * the classical Metropolis algorithm"), for dQ in {-2, 0, 2} and dBV, dBJ in
  * [-20, 20]: out[((dQ + 2)/2 * 41 + dBV + 20) * 41 + dBJ + 20] =

@@ -1,10 +1,11 @@
 """Build ``libccmc.so`` in-tree (``paper_2301_11735_gb300/_build``) for sm_103a.
 
-Three translation units are compiled in parallel and linked into one shared
+Four translation units are compiled in parallel and linked into one shared
 library that exports the C ABI of ``include/ccmc.h``:
 
 * ``csrc/ccmc_kernels.cu`` -- the CUDA kernels (nvcc, sm_103a only);
 * ``csrc/ccmc_api.cu``     -- host code of the C ABI (nvcc host pass);
+* ``csrc/ccmc_noalloc.cu`` -- the recount entry point that allocates nothing;
 * ``csrc/ccmc_tables.cpp`` -- FP64 threshold tables (g++).
 
 All host code is compiled with ``-ffp-contract=off`` so the threshold tables
@@ -61,6 +62,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     jobs = {
         "ccmc_kernels.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_kernels.cu")],
         "ccmc_api.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_api.cu")],
+        "ccmc_noalloc.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_noalloc.cu")],
         "ccmc_tables.o": [os.environ.get("CXX", "g++"), "-c", "-std=c++17", "-O2", "-fPIC",
                           "-ffp-contract=off", f"-I{cuda}/include",
                           os.path.join(CSRC, "ccmc_tables.cpp")],
