@@ -95,6 +95,34 @@ int ccmc_sweep(ccmc_lattice *h, int64_t nsweeps, double beta, double Delta, doub
  * sweep count of a record is the completed phases / 8.  Errors as ccmc_sweep. */
 int ccmc_phases(ccmc_lattice *h, int64_t nphases, double beta, double Delta, double V, double J);
 
+/* ---- Batches of replicas (several independent lattices of uneven size). ----
+ * A batch groups existing, initialised lattices (each with its own size,
+ * seed and parameters; Sec. 3.2 runs "several copies of the lattice").
+ * ccmc_batch_sweep advances lattice i by nsweeps[i] sweeps at (beta[i],
+ * Delta[i], V[i], J[i]).  Lattices of at most resident_max_sites sites run
+ * together in one persistent launch on the batch stream: each CTA keeps a
+ * whole lattice and its tables in shared memory and runs all its sweeps,
+ * taking lattices from a work queue largest first.  Larger lattices run the
+ * per-phase path on their own streams at the same time.  Every lattice ends in
+ * exactly the state ccmc_sweep would give it (same random streams), and its
+ * observable ring gets the same records.  Ordering: the batch waits for work
+ * already queued on each lattice's stream, and each lattice's stream waits for
+ * the batch.  Errors: E_INVAL, E_STATE (a lattice not initialised, or left in
+ * the middle of a sweep by ccmc_phases). */
+typedef struct ccmc_batch ccmc_batch;
+int ccmc_batch_create(int count, ccmc_lattice *const *lattices, void *cuda_stream,
+                      ccmc_batch **out);
+int ccmc_batch_destroy(ccmc_batch *b);
+/* Launch shape of the resident launch (autotuner knobs; results do not depend
+ * on them): threads per CTA (64, 128 or 256), the largest lattice (in sites)
+ * kept in shared memory, and CTAs per SM of the persistent grid. */
+int ccmc_batch_config(ccmc_batch *b, int resident_threads, int64_t resident_max_sites,
+                      int ctas_per_sm);
+int ccmc_batch_sweep(ccmc_batch *b, const int64_t *nsweeps, const double *beta,
+                     const double *Delta, const double *V, const double *J, int obs_every);
+/* Wait for the batch stream and every member's stream; reports device errors. */
+int ccmc_batch_sync(ccmc_batch *b);
+
 /* Recount the current lattice and return its observables (synchronises). */
 int ccmc_observables(ccmc_lattice *h, ccmc_obs *out);
 /* Copy the ring's records, oldest first, into out[0 .. cap); *n_written gets

@@ -63,6 +63,12 @@ def _load():
         "ccmc_set_state": (c_int, [vp, u8p, c_uint64, c_int64]),
         "ccmc_sync": (c_int, [vp]),
         "ccmc_philox_device": (c_int, [c_uint32] * 6 + [c_int64, u32p]),
+        "ccmc_batch_create": (c_int, [c_int, POINTER(vp), vp, POINTER(vp)]),
+        "ccmc_batch_destroy": (c_int, [vp]),
+        "ccmc_batch_config": (c_int, [vp, c_int, c_int64, c_int]),
+        "ccmc_batch_sweep": (c_int, [vp, i64p, POINTER(c_double), POINTER(c_double),
+                                     POINTER(c_double), POINTER(c_double), c_int]),
+        "ccmc_batch_sync": (c_int, [vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -197,3 +203,52 @@ class Lattice:
         assert st.shape == (self.Ly, self.Lx)
         _check(lib().ccmc_set_state(self._h, st.ctypes.data_as(POINTER(ctypes.c_uint8)),
                                    seed & (2 ** 64 - 1), sweeps_done), "ccmc_set_state")
+
+
+class Batch:
+    """Several lattices swept together (ccmc_batch_*): small ones share one
+    persistent shared-memory-resident launch, large ones run alongside."""
+
+    def __init__(self, lattices, stream=None):
+        self.lattices = list(lattices)
+        arr = (c_void_p * len(self.lattices))(*[lat.handle.value for lat in self.lattices])
+        h = c_void_p()
+        _check(lib().ccmc_batch_create(len(self.lattices), arr, _stream_handle(stream),
+                                       ctypes.byref(h)), "ccmc_batch_create")
+        self._h = h
+
+    def config(self, threads: int = 256, resident_max_sites: int = 1 << 18, ctas_per_sm: int = 2):
+        _check(lib().ccmc_batch_config(self._h, threads, resident_max_sites, ctas_per_sm),
+               "ccmc_batch_config")
+
+    def sweep(self, nsweeps, beta, Delta, V, J, obs_every: int = 0):
+        n = len(self.lattices)
+
+        def arr(x, dt):
+            a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=dt), (n,)))
+            return a
+
+        ns, b, d, v, j = (arr(nsweeps, np.int64), arr(beta, np.float64), arr(Delta, np.float64),
+                          arr(V, np.float64), arr(J, np.float64))
+        dp = POINTER(c_double)
+        _check(lib().ccmc_batch_sweep(self._h, ns.ctypes.data_as(POINTER(c_int64)),
+                                      b.ctypes.data_as(dp), d.ctypes.data_as(dp),
+                                      v.ctypes.data_as(dp), j.ctypes.data_as(dp), obs_every),
+               "ccmc_batch_sweep")
+
+    def sync(self):
+        _check(lib().ccmc_batch_sync(self._h), "ccmc_batch_sync")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ccmc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -81,7 +82,8 @@ void drop_graphs(ccmc_lattice *h) {
   h->graphs.clear();
 }
 
-int upload_params(ccmc_lattice *h, double beta, double Delta, double V, double J) {
+int upload_params_on(ccmc_lattice *h, double beta, double Delta, double V, double J,
+                     cudaStream_t st) {
   if (h->have_params && h->params[0] == beta && h->params[1] == Delta && h->params[2] == V &&
       h->params[3] == J)
     return CCMC_OK;
@@ -90,8 +92,8 @@ int upload_params(ccmc_lattice *h, double beta, double Delta, double V, double J
   build_thresholds(beta, Delta, V, J, thr32.data());
   for (int i = 0; i < kTableN; ++i) thr16[i] = (uint16_t)(thr32[i] >> 16);
   CK(cudaMemcpyAsync(h->t.thr32, thr32.data(), sizeof(uint32_t) * kTableN,
-                     cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(h->t.thr16, thr16.data(), kThr16Bytes, cudaMemcpyHostToDevice, h->stream));
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->t.thr16, thr16.data(), kThr16Bytes, cudaMemcpyHostToDevice, st));
   // pageable sources: the copies are staged before the calls return
   h->have_params = true;
   h->params[0] = beta;
@@ -99,6 +101,10 @@ int upload_params(ccmc_lattice *h, double beta, double Delta, double V, double J
   h->params[2] = V;
   h->params[3] = J;
   return CCMC_OK;
+}
+
+int upload_params(ccmc_lattice *h, double beta, double Delta, double V, double J) {
+  return upload_params_on(h, beta, Delta, V, J, h->stream);
 }
 
 // Queue `sweeps` sweeps starting at phase offset 0 of the control block's base;
@@ -471,6 +477,197 @@ int ccmc_set_state(ccmc_lattice *h, const uint8_t *host_in, uint64_t seed, int64
   }
   h->phases_done = 8 * sweeps_done;
   h->initialised = true;
+  return CCMC_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Batches: many lattices swept together.  Lattices whose packed words fit the
+// resident limit run in one persistent resident_kernel launch on the batch
+// stream (each CTA holds a whole lattice in shared memory); larger ones run the
+// per-phase path on their own streams at the same time.
+struct ccmc_batch {
+  std::vector<ccmc_lattice *> lats;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  JobDesc *d_jobs = nullptr;
+  int *d_queue = nullptr;
+  int threads = 256;
+  int64_t resident_max_sites = (int64_t)1 << 18;
+  int ctas_per_sm = 2;
+  int sms = 152;
+  cudaEvent_t ev = nullptr;
+  std::vector<cudaEvent_t> lat_ev;
+};
+
+namespace {
+JobDesc job_of(ccmc_lattice *h, int64_t nsweeps, int obs_every) {
+  JobDesc d{};
+  d.g = h->g;
+  d.thr16 = reinterpret_cast<const uint32_t *>(h->t.thr16);
+  d.thr32 = h->t.thr32;
+  d.trans_far = h->t.trans_far;
+  d.trans_near = h->t.trans_near;
+  d.nsweeps = nsweeps;
+  d.ring = h->d_ring;
+  d.ring_cap = h->ring_cap;
+  d.hist = h->d_hist;
+  d.nbins = h->nbins;
+  d.obs_every = obs_every;
+  return d;
+}
+}  // namespace
+
+extern "C" {
+
+int ccmc_batch_create(int count, ccmc_lattice *const *lattices, void *cuda_stream,
+                      ccmc_batch **out) {
+  if (!out || count < 1 || !lattices) return CCMC_E_INVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i)
+    if (!lattices[i]) return CCMC_E_INVAL;
+  ccmc_batch *b = new (std::nothrow) ccmc_batch();
+  if (!b) return CCMC_E_NOMEM;
+  b->lats.assign(lattices, lattices + count);
+  auto fail = [&](int code) {
+    ccmc_batch_destroy(b);
+    return code;
+  };
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(CCMC_E_CUDA);
+    b->own_stream = true;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int64_t max_words = optin / 4 - kResTableWords - 64;
+  if (b->resident_max_sites / 4 > max_words) b->resident_max_sites = max_words * 4;
+  if (cudaMalloc(&b->d_jobs, sizeof(JobDesc) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_queue, sizeof(int)) != cudaSuccess)
+    return fail(CCMC_E_NOMEM);
+  if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
+    return fail(CCMC_E_CUDA);
+  b->lat_ev.assign(count, nullptr);
+  for (auto &e : b->lat_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return fail(CCMC_E_CUDA);
+  *out = b;
+  return CCMC_OK;
+}
+
+int ccmc_batch_destroy(ccmc_batch *b) {
+  if (!b) return CCMC_E_INVAL;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_queue);
+  if (b->ev) cudaEventDestroy(b->ev);
+  for (auto e : b->lat_ev)
+    if (e) cudaEventDestroy(e);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return CCMC_OK;
+}
+
+int ccmc_batch_config(ccmc_batch *b, int resident_threads, int64_t resident_max_sites,
+                      int ctas_per_sm) {
+  if (!b) return CCMC_E_INVAL;
+  if (resident_threads != 64 && resident_threads != 128 && resident_threads != 256)
+    return CCMC_E_INVAL;
+  if (resident_max_sites < 0 || ctas_per_sm < 1 || ctas_per_sm > 32) return CCMC_E_INVAL;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int64_t max_words = optin / 4 - kResTableWords - 64;
+  if (resident_max_sites / 4 > max_words) return CCMC_E_INVAL;
+  b->threads = resident_threads;
+  b->resident_max_sites = resident_max_sites;
+  b->ctas_per_sm = ctas_per_sm;
+  return CCMC_OK;
+}
+
+int ccmc_batch_sweep(ccmc_batch *b, const int64_t *nsweeps, const double *beta,
+                     const double *Delta, const double *V, const double *J, int obs_every) {
+  if (!b || !nsweeps || !beta || !Delta || !V || !J) return CCMC_E_INVAL;
+  const int n = (int)b->lats.size();
+  for (int i = 0; i < n; ++i) {
+    if (nsweeps[i] < 0 || !(beta[i] >= 0.0) || !std::isfinite(Delta[i]) ||
+        !std::isfinite(V[i]) || !std::isfinite(J[i]))
+      return CCMC_E_INVAL;
+    ccmc_lattice *h = b->lats[i];
+    if (!h->initialised || h->phases_done % 8) return CCMC_E_STATE;
+    for (int k = 0; k < i; ++k)
+      if (b->lats[k] == h) return CCMC_E_INVAL;  // a lattice may appear once
+  }
+  std::vector<JobDesc> jobs;
+  std::vector<int> resident;
+  for (int i = 0; i < n; ++i) {
+    ccmc_lattice *h = b->lats[i];
+    const int64_t sites = 16 * h->g.cstride * 16;  // padded sites held in words
+    if (nsweeps[i] == 0 || sites > b->resident_max_sites) continue;
+    // order the batch stream after work already queued on this lattice's stream
+    if (h->stream != b->stream) {
+      CK(cudaEventRecord(b->lat_ev[i], h->stream));
+      CK(cudaStreamWaitEvent(b->stream, b->lat_ev[i], 0));
+    }
+    int rc = upload_params_on(h, beta[i], Delta[i], V[i], J[i], b->stream);
+    if (rc) return rc;
+    jobs.push_back(job_of(h, nsweeps[i], obs_every));
+    resident.push_back(i);
+  }
+  if (!jobs.empty()) {
+    // largest first: the queue hands the longest jobs out before the short ones
+    std::vector<int> order(jobs.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+      const int64_t wx = (int64_t)jobs[x].g.Lx * jobs[x].g.Ly * jobs[x].nsweeps;
+      const int64_t wy = (int64_t)jobs[y].g.Lx * jobs[y].g.Ly * jobs[y].nsweeps;
+      return wx > wy;
+    });
+    std::vector<JobDesc> sorted;
+    int64_t max_words = 0;
+    for (int k : order) {
+      sorted.push_back(jobs[k]);
+      const int64_t w = 16 * jobs[k].g.cstride;
+      if (w > max_words) max_words = w;
+    }
+    CK(cudaMemcpyAsync(b->d_jobs, sorted.data(), sizeof(JobDesc) * sorted.size(),
+                       cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream));
+    int grid = b->sms * b->ctas_per_sm;
+    if (grid > (int)sorted.size()) grid = (int)sorted.size();
+    CK(launch_resident(b->d_jobs, (int)sorted.size(), b->d_queue, grid, b->threads, max_words,
+                       b->stream));
+    CK(cudaEventRecord(b->ev, b->stream));
+    for (int i : resident) {
+      ccmc_lattice *h = b->lats[i];
+      h->phases_done += 8 * nsweeps[i];
+      if (h->stream != b->stream) CK(cudaStreamWaitEvent(h->stream, b->ev, 0));
+    }
+  }
+  // the rest on their own streams, overlapping the resident launch
+  for (int i = 0; i < n; ++i) {
+    ccmc_lattice *h = b->lats[i];
+    const int64_t sites = 16 * h->g.cstride * 16;
+    if (nsweeps[i] == 0 || sites <= b->resident_max_sites) continue;
+    const int rc = ccmc_sweep(h, nsweeps[i], beta[i], Delta[i], V[i], J[i], obs_every);
+    if (rc) return rc;
+  }
+  return CCMC_OK;
+}
+
+int ccmc_batch_sync(ccmc_batch *b) {
+  if (!b) return CCMC_E_INVAL;
+  CK(cudaStreamSynchronize(b->stream));
+  for (ccmc_lattice *h : b->lats) {
+    const int rc = check_status(h);
+    if (rc) return rc;
+  }
   return CCMC_OK;
 }
 

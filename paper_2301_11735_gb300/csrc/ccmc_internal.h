@@ -56,6 +56,24 @@ struct LaunchCfg {
   int phase_grid_cap = 152 * 8;
 };
 
+// One lattice of a resident batch launch (device array, filled on the host).
+struct JobDesc {
+  Geo g;                    // the lattice in global memory
+  const uint32_t *thr16;    // its tables
+  const uint32_t *thr32;
+  const uint32_t *trans_far;
+  const uint32_t *trans_near;
+  int64_t nsweeps;          // sweeps to run in this launch
+  int64_t *ring;            // observable ring (records every obs_every sweeps)
+  int64_t ring_cap;
+  int64_t *hist;            // histograms (nullptr: none)
+  int nbins;
+  int obs_every;
+};
+
+// Shared memory of the resident kernel besides the lattice words.
+constexpr int kResTableWords = ((kTableN + 1) / 2 + 1) / 2 * 2 + 4 * kTransN;
+
 // Host-side table builders (ccmc_tables.cpp).
 void build_thresholds(double beta, double Delta, double V, double J, uint32_t *thr32);
 // Returns false if some entry could index outside the threshold table.
@@ -72,6 +90,11 @@ cudaError_t launch_advance(int64_t *ctl, int64_t phases, cudaStream_t s);
 cudaError_t launch_set_ctl(int64_t *ctl, int64_t phase_base, cudaStream_t s);
 cudaError_t launch_unpack(const Geo &g, uint8_t *out, cudaStream_t s);
 cudaError_t launch_pack(const Geo &g, const uint8_t *in, int *bad, cudaStream_t s);
+// Resident batch kernel: grid CTAs of `threads` threads take jobs from *queue
+// (zeroed by the caller) until njobs are done; max_words bounds 16 Cy W.
+cudaError_t launch_resident(const JobDesc *d_jobs, int njobs, int *d_queue, int grid, int threads,
+                            int64_t max_words, cudaStream_t s);
+int64_t resident_smem_bytes(int64_t max_words);
 cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                           uint32_t k1, int64_t count, uint32_t *out, cudaStream_t s);
 

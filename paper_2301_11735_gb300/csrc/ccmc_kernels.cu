@@ -139,8 +139,9 @@ __device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, in
 }
 
 template <bool kAligned>
-__device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const PhaseSmem &sm,
-                                           const uint32_t *thr32, int j, int w, uint64_t P) {
+__device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
+                                           const uint32_t *thr16, const uint32_t *thr32, int j,
+                                           int w, uint64_t P) {
   const int s0 = w << 4;
   const int n = kAligned ? 16 : min(16, g.Cx - s0);
   const int Cy = g.Cy;
@@ -196,9 +197,9 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
       const uint32_t pc = (((t & 1) ? pcO : pcE) >> (4 * (t >> 1))) & 15u;
       const uint32_t v = R & 0xFFFFu, uh = R >> 16;
       const uint32_t r12 = v - 12u * ((v * 43691u) >> 19);  // v mod 12 for v < 2^16
-      const uint2 e = sm.trans[pc * 12u + r12];
+      const uint2 e = trans[pc * 12u + r12];
       const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
-      const uint32_t th = (sm.thr16[idx >> 1] >> (16 * (idx & 1))) & 0xFFFFu;
+      const uint32_t th = (thr16[idx >> 1] >> (16 * (idx & 1))) & 0xFFFFu;
       if (v >= 65532u || uh == th) {
         slow |= 1u << t;
       } else if (uh < th) {
@@ -232,7 +233,7 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
       r = sl.y % 12u;
     else
       continue;  // keep the current configuration
-    const uint2 e = sm.trans[pc * 12u + r];
+    const uint2 e = trans[pc * 12u + r];
     const int sh = 4 * (t >> 1);
     const uint32_t sa4 = (((t & 1) ? sa.so : sa.se) >> sh) & 15u;
     const uint32_t sb4 = (((t & 1) ? sb.so : sb.se) >> sh) & 15u;
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(256) phase_kernel(Geo g, const uint32_t *thr16
   int j = wid / g.W, w = wid - j * g.W;
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
-    phase_word<kAligned>(g, u, sm, thr32, j, w, P);
+    phase_word<kAligned>(g, u, sm.trans, sm.thr16, thr32, j, w, P);
     w += sw;
     j += sj;
     if (w >= g.W) {
@@ -329,11 +330,12 @@ __device__ __forceinline__ int64_t warp_sum(int64_t v) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
-  int c[7] = {0, 0, 0, 0, 0, 0, 0};  // Nc, BV, BJ, M, Ms, S, Ss
+// Adds the observables of class words tid, tid + nthreads, ... to c[7]
+// (Nc, BV, BJ, M, M_stag, S_sum, S_stag): popcounts of the charge and sign bit
+// planes against the right and down neighbour windows.
+__device__ __forceinline__ void count_words(const Geo &g, int64_t tid, int64_t nthreads, int c[7]) {
   const int64_t nwords = 16 * g.cstride;
-  for (int64_t wid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; wid < nwords;
-       wid += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t wid = tid; wid < nwords; wid += nthreads) {
     const int cls = (int)(wid / g.cstride);
     const int64_t rem = wid - (int64_t)cls * g.cstride;
     const int j = (int)(rem / g.W), w = (int)(rem - (int64_t)j * g.W);
@@ -367,6 +369,12 @@ __global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
       c[2] += __popc(UU & ~diff) - __popc(UU & diff);
     }
   }
+}
+
+__global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
+  int c[7] = {0, 0, 0, 0, 0, 0, 0};  // Nc, BV, BJ, M, Ms, S, Ss
+  count_words(g, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+              c);
   __shared__ int64_t red[8][7];
   __shared__ bool last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -418,6 +426,119 @@ __global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
     }
     g.ctl[kCtlTicket] = 0;
   }
+}
+
+// ============================================================================
+// Resident batch kernel (many lattices of uneven size, one persistent launch).
+// Each CTA takes lattices from a work queue, largest first; it holds the whole
+// packed lattice and its tables in shared memory and runs all of that lattice's
+// sweeps with block barriers between phases, recounting into the lattice's ring
+// when due; then it writes the lattice back and takes the next one.  The same
+// per-word code as phase_kernel runs against shared memory, so results are
+// identical to the per-phase launches.
+__global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict__ jobs, int njobs,
+                                                       int *queue) {
+  extern __shared__ __align__(16) uint32_t dyn[];
+  uint32_t *s_thr16 = dyn;
+  uint2 *s_far = reinterpret_cast<uint2 *>(dyn + ((kTableN + 1) / 2 + 1) / 2 * 2);
+  uint2 *s_near = s_far + kTransN;
+  uint32_t *s_words = dyn + kResTableWords;
+  __shared__ Sched s_sched;
+  __shared__ int s_job;
+  __shared__ int64_t s_red[32][7];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = atomicAdd(queue, 1);
+    __syncthreads();
+    const int job = s_job;
+    if (job >= njobs) break;
+    const JobDesc &J = jobs[job];
+    const Geo g = J.g;
+    const int64_t nw = 16 * g.cstride;
+    for (int t = threadIdx.x; t < (kTableN + 1) / 2; t += blockDim.x) s_thr16[t] = J.thr16[t];
+    for (int t = threadIdx.x; t < kTransN; t += blockDim.x) {
+      s_far[t] = make_uint2(J.trans_far[2 * t], J.trans_far[2 * t + 1]);
+      s_near[t] = make_uint2(J.trans_near[2 * t], J.trans_near[2 * t + 1]);
+    }
+    for (int64_t t = threadIdx.x; t < nw; t += blockDim.x) s_words[t] = g.words[t];
+    const int64_t P0 = g.ctl[kCtlPhaseBase];
+    const int64_t nsweeps = J.nsweeps;
+    const int obs_every = J.obs_every;
+    Geo gs = g;
+    gs.words = s_words;
+    const bool aligned = (g.Cx & 15) == 0;
+    const int nwa = g.Cy * g.W;  // a-words per phase
+    __syncthreads();
+    for (int64_t s = 0; s < nsweeps; ++s) {
+      for (int p = 0; p < 8; ++p) {
+        const uint64_t P = (uint64_t)(P0 + 8 * s + p);
+        if (threadIdx.x < 32) {
+          const Sched sc = draw_schedule(gs, P);
+          if (threadIdx.x == 0) s_sched = sc;
+        }
+        __syncthreads();
+        const Sched sc = s_sched;
+        const PhaseU u = phase_uniform(gs, sc);
+        const uint2 *tr = sc.near ? s_near : s_far;
+        for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
+          const int j = wid / g.W, w = wid - j * g.W;
+          if (aligned)
+            phase_word<true>(gs, u, tr, s_thr16, J.thr32, j, w, P);
+          else
+            phase_word<false>(gs, u, tr, s_thr16, J.thr32, j, w, P);
+        }
+        __syncthreads();
+      }
+      const int64_t done = P0 / 8 + s + 1;
+      if (obs_every > 0 && done % obs_every == 0) {
+        int c[7] = {0, 0, 0, 0, 0, 0, 0};
+        count_words(gs, threadIdx.x, blockDim.x, c);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+          const int64_t v = warp_sum((int64_t)c[k]);
+          if (lane == 0) s_red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          int64_t rec[8];
+          rec[0] = done;
+          for (int k = 0; k < 7; ++k) {
+            int64_t v = 0;
+            for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) v += s_red[wv][k];
+            rec[1 + k] = v;
+          }
+          for (int k = 0; k < 8; ++k) g.ctl[kCtlLatest + k] = rec[k];
+          const int64_t cnt = g.ctl[kCtlObsCount];
+          int64_t *dst = J.ring + (cnt % J.ring_cap) * 8;
+          for (int k = 0; k < 8; ++k) dst[k] = rec[k];
+          g.ctl[kCtlObsCount] = cnt + 1;
+          if (J.hist) {
+            const int64_t N = (int64_t)g.Lx * g.Ly;
+            const int64_t vals[3] = {rec[4], rec[5], rec[7]};
+            for (int h = 0; h < 3; ++h) J.hist[h * J.nbins + (vals[h] + N) * J.nbins / (2 * N + 1)] += 1;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int64_t t = threadIdx.x; t < nw; t += blockDim.x) g.words[t] = s_words[t];
+    if (threadIdx.x == 0) g.ctl[kCtlPhaseBase] = P0 + 8 * nsweeps;
+    __syncthreads();
+  }
+}
+
+int64_t resident_smem_bytes(int64_t max_words) {
+  return (int64_t)sizeof(uint32_t) * (kResTableWords + max_words);
+}
+
+cudaError_t launch_resident(const JobDesc *d_jobs, int njobs, int *d_queue, int grid, int threads,
+                            int64_t max_words, cudaStream_t s) {
+  const int64_t smem = resident_smem_bytes(max_words);
+  cudaError_t e = cudaFuncSetAttribute(resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  resident_kernel<<<grid, threads, (size_t)smem, s>>>(d_jobs, njobs, d_queue);
+  return cudaGetLastError();
 }
 
 // ============================================================================

@@ -1,0 +1,139 @@
+"""Batched replicas: many lattices of uneven size in one persistent launch.
+
+Each lattice of a batch must end bit-identical to the same lattice advanced on
+its own with ccmc_sweep (and, for small ones, to the oracle), with identical
+observable records, whatever the launch shape the autotuner picks.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+MIX = [(4, 4), (16, 16), (20, 12), (32, 32), (36, 44), (64, 64), (68, 20), (128, 128),
+       (256, 256), (132, 8)]
+
+
+@pytest.fixture(scope="module")
+def cc():
+    import paper_2301_11735_gb300 as cc
+
+    return cc
+
+
+def _params(i):
+    T = 0.3 + 0.17 * i
+    return (1.0 / T, [-0.5, 0.0, 0.5][i % 3], 1.0, [1.0, 0.5][i % 2])
+
+
+def _make(cc, shapes, seed0=100):
+    lats = []
+    for i, (Lx, Ly) in enumerate(shapes):
+        lat = cc.Lattice(Lx, Ly, obs_capacity=256)
+        lat.init_constrained(seed0 + i, [0.0, 0.1, -0.2, 0.3][i % 4], 0.3)
+        lats.append(lat)
+    return lats
+
+
+def _run_batch(cc, shapes, nsweeps, obs_every, cfg=None, calls=1):
+    lats = _make(cc, shapes)
+    with cc.Batch(lats) as b:
+        if cfg:
+            b.config(*cfg)
+        P = [_params(i) for i in range(len(shapes))]
+        for _ in range(calls):
+            b.sweep(nsweeps, [p[0] for p in P], [p[1] for p in P], [p[2] for p in P],
+                    [p[3] for p in P], obs_every=obs_every)
+        b.sync()
+    out = [(lat.get_state(), lat.obs_series()) for lat in lats]
+    for lat in lats:
+        lat.close()
+    return out
+
+
+def _run_single(cc, shapes, nsweeps, obs_every, calls=1):
+    lats = _make(cc, shapes)
+    out = []
+    for i, lat in enumerate(lats):
+        for _ in range(calls):
+            lat.sweep(nsweeps[i], *_params(i), obs_every=obs_every)
+        out.append((lat.get_state(), lat.obs_series()))
+        lat.close()
+    return out
+
+
+def test_batch_equals_individual_sweeps_and_oracle(cc):
+    nsw = [11 + 3 * i for i in range(len(MIX))]
+    got = _run_batch(cc, MIX, nsw, obs_every=2)
+    ref = _run_single(cc, MIX, nsw, obs_every=2)
+    for i, ((s1, r1), (s2, r2)) in enumerate(zip(got, ref)):
+        assert np.array_equal(s1, s2), MIX[i]
+        assert np.array_equal(r1, r2), MIX[i]
+    for i in (0, 1, 2, 4, 6):
+        Lx, Ly = MIX[i]
+        st = oracle.init_constrained(Lx, Ly, 100 + i, [0.0, 0.1, -0.2, 0.3][i % 4], 0.3)
+        rec = oracle.sweeps(st, 100 + i, 0, nsw[i], *_params(i), obs_every=2)
+        assert np.array_equal(got[i][0], st) and np.array_equal(got[i][1], rec), MIX[i]
+
+
+@pytest.mark.parametrize("cfg", [(64, 1 << 17, 1), (128, 1 << 17, 4), (256, 1 << 17, 8),
+                                 (256, 4096, 2)])
+def test_batch_results_do_not_depend_on_launch_shape(cc, cfg):
+    """Launch shapes the autotuner may pick, including a resident limit that
+    sends the larger lattices down the per-phase path."""
+    nsw = [7] * len(MIX)
+    base = _run_batch(cc, MIX, nsw, obs_every=3)
+    got = _run_batch(cc, MIX, nsw, obs_every=3, cfg=cfg)
+    for i, ((s1, r1), (s2, r2)) in enumerate(zip(got, base)):
+        assert np.array_equal(s1, s2) and np.array_equal(r1, r2), (cfg, MIX[i])
+
+
+def test_batch_continues_across_calls(cc):
+    nsw = [5] * len(MIX)
+    two = _run_batch(cc, MIX, nsw, obs_every=1, calls=2)
+    one = _run_single(cc, MIX, [10] * len(MIX), obs_every=1)
+    for (s1, r1), (s2, r2) in zip(two, one):
+        assert np.array_equal(s1, s2) and np.array_equal(r1, r2)
+
+
+def test_replica_workload_sample(cc):
+    """A sample of the 512-replica workload (L in {32, 64, 128, 256}, T grid,
+    n and Delta drawn per replica): batched == one by one."""
+    from workloads import replicas_512
+
+    sims = replicas_512(nsweeps=40)[:48]
+    lats = []
+    for s in sims:
+        lat = cc.Lattice(s.Lx, s.Ly)
+        lat.init_constrained(s.seed, s.n, s.charged_frac)
+        lats.append(lat)
+    with cc.Batch(lats) as b:
+        b.sweep([s.nsweeps for s in sims], [s.beta for s in sims], [s.Delta for s in sims],
+                [s.V for s in sims], [s.J for s in sims], obs_every=10)
+        b.sync()
+    for s, lat in zip(sims, lats):
+        with cc.Lattice(s.Lx, s.Ly) as one:
+            one.init_constrained(s.seed, s.n, s.charged_frac)
+            one.sweep(s.nsweeps, s.beta, s.Delta, s.V, s.J, obs_every=10)
+            assert np.array_equal(one.get_state(), lat.get_state())
+            assert np.array_equal(one.obs_series(), lat.obs_series())
+        lat.close()
+
+
+def test_batch_rejects_bad_use(cc):
+    a = cc.Lattice(16, 16)
+    b_ = cc.Lattice(16, 16)
+    with pytest.raises(cc.CcmcError):
+        with cc.Batch([a, b_]) as b:  # b_ never initialised
+            a.init_constrained(1, 0.0)
+            b.sweep(2, 1.0, 0.0, 1.0, 1.0)
+    b_.init_constrained(2, 0.0)
+    a.phases(3, 1.0, 0.0, 1.0, 1.0)  # a is now mid-sweep
+    with cc.Batch([a, b_]) as b:
+        with pytest.raises(cc.CcmcError):
+            b.sweep(2, 1.0, 0.0, 1.0, 1.0)
+        with pytest.raises(cc.CcmcError):
+            b.config(100, 1 << 16, 2)
+    a.close()
+    b_.close()
