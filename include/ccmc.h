@@ -46,6 +46,7 @@ extern "C" {
 #define CCMC_E_BUDGET (-5)  /* admission refused: the memory budget is full    */
 #define CCMC_E_STATE (-6)   /* call out of order (e.g. sweep before init)      */
 #define CCMC_E_NOTFOUND (-7)/* unknown ticket or handle                        */
+#define CCMC_PENDING 1      /* ccmc_server_poll: the request has not finished   */
 
 /* Observables after a sweep (Sec. 2.2 and Eq. 3).  All integer terms are exact
  * recounts of the lattice: Nc = sum S^2, BV = sum_bonds S S, BJ = sum_bonds
@@ -122,6 +123,61 @@ int ccmc_batch_sweep(ccmc_batch *b, const int64_t *nsweeps, const double *beta,
                      const double *Delta, const double *V, const double *J, int obs_every);
 /* Wait for the batch stream and every member's stream; reports device errors. */
 int ccmc_batch_sync(ccmc_batch *b);
+
+/* ---- Serving: a continuous-batching request loop of independent runs. ----
+ * A request is one simulation: an Lx x Ly lattice initialised as by
+ * ccmc_init_constrained(seed, n, charged_frac), then nsweeps sweeps at
+ * (beta, Delta, V, J), recording observables every obs_every sweeps (0: none).
+ * state_out, if not NULL, is a host buffer of Lx * Ly bytes that receives the
+ * final lattice; it must stay valid until the request finishes.  Requests are
+ * admitted first come first served while fewer than max_active are running and
+ * their device memory fits the budget (a request that can never fit finishes
+ * with E_BUDGET).  Admitted simulations stay resident on the GPU; a scheduler
+ * thread advances all of them in slices of about slice_ms (each slice is one
+ * batched launch, ccmc_batch_*), so requests that arrive while others run
+ * join at the next slice and leave as soon as they are done.  Results equal
+ * those of running each request alone.  Times are seconds since the server
+ * started (host clock). */
+typedef struct {
+  int Lx, Ly;
+  uint64_t seed;
+  double n, charged_frac;
+  int64_t nsweeps;
+  double beta, Delta, V, J;
+  int obs_every;
+  uint8_t *state_out;
+} ccmc_request;
+
+typedef struct {
+  int status;            /* CCMC_OK or the error that ended the request */
+  ccmc_obs final_obs;    /* observables after the last sweep            */
+  int64_t site_updates;  /* Lx * Ly * nsweeps                           */
+  double submit_s, start_s, done_s;
+} ccmc_result;
+
+typedef struct {
+  int64_t submitted, queued, active, completed, rejected, failed, slices, site_updates,
+      bytes_in_use;
+} ccmc_server_stats;
+
+typedef struct ccmc_server ccmc_server;
+int ccmc_server_start(size_t hbm_budget_bytes, int max_active, double slice_ms,
+                      ccmc_server **out);
+int ccmc_server_submit(ccmc_server *s, const ccmc_request *req, uint64_t *ticket);
+/* CCMC_OK and *out filled once the request finished, CCMC_PENDING before,
+ * E_NOTFOUND for an unknown (or released) ticket. */
+int ccmc_server_poll(ccmc_server *s, uint64_t ticket, ccmc_result *out);
+/* Block up to timeout_s seconds for the request; E_TIMEOUT if it is not done. */
+int ccmc_server_wait(ccmc_server *s, uint64_t ticket, ccmc_result *out, double timeout_s);
+/* Observable records of a finished request (as ccmc_obs_series). */
+int ccmc_server_series(ccmc_server *s, uint64_t ticket, ccmc_obs *out, int64_t cap,
+                       int64_t *n_written);
+/* Forget a finished request's result. */
+int ccmc_server_release(ccmc_server *s, uint64_t ticket);
+int ccmc_server_stats_get(ccmc_server *s, ccmc_server_stats *out);
+/* Stop accepting requests, finish every queued and running one, then free
+ * everything. */
+int ccmc_server_stop(ccmc_server *s);
 
 /* Recount the current lattice and return its observables (synchronises). */
 int ccmc_observables(ccmc_lattice *h, ccmc_obs *out);

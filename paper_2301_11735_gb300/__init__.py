@@ -22,6 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libccmc.so")
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUDGET, E_STATE, E_NOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
+PENDING = 1
 TABLE_N = 3 * 41 * 41
 OBS_FIELDS = ("sweeps_done", "Nc", "BV", "BJ", "M", "M_stag", "S_sum", "S_stag", "E")
 
@@ -37,6 +38,29 @@ class Obs(ctypes.Structure):
 
     def as_dict(self):
         return {n: getattr(self, n) for n in OBS_FIELDS}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("Lx", c_int), ("Ly", c_int), ("seed", c_uint64), ("n", c_double),
+                ("charged_frac", c_double), ("nsweeps", c_int64), ("beta", c_double),
+                ("Delta", c_double), ("V", c_double), ("J", c_double), ("obs_every", c_int),
+                ("state_out", c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", c_int), ("final_obs", Obs), ("site_updates", c_int64),
+                ("submit_s", c_double), ("start_s", c_double), ("done_s", c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k in ("status", "site_updates", "submit_s", "start_s",
+                                            "done_s")}
+        d["final_obs"] = self.final_obs.as_dict()
+        return d
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, c_int64) for k in ("submitted", "queued", "active", "completed", "rejected",
+                                       "failed", "slices", "site_updates", "bytes_in_use")]
 
 
 def _load():
@@ -69,6 +93,14 @@ def _load():
         "ccmc_batch_sweep": (c_int, [vp, i64p, POINTER(c_double), POINTER(c_double),
                                      POINTER(c_double), POINTER(c_double), c_int]),
         "ccmc_batch_sync": (c_int, [vp]),
+        "ccmc_server_start": (c_int, [ctypes.c_size_t, c_int, c_double, POINTER(vp)]),
+        "ccmc_server_submit": (c_int, [vp, POINTER(Request), POINTER(c_uint64)]),
+        "ccmc_server_poll": (c_int, [vp, c_uint64, POINTER(Result)]),
+        "ccmc_server_wait": (c_int, [vp, c_uint64, POINTER(Result), c_double]),
+        "ccmc_server_series": (c_int, [vp, c_uint64, POINTER(Obs), c_int64, i64p]),
+        "ccmc_server_release": (c_int, [vp, c_uint64]),
+        "ccmc_server_stats_get": (c_int, [vp, POINTER(ServerStats)]),
+        "ccmc_server_stop": (c_int, [vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -217,9 +249,18 @@ class Batch:
                                        ctypes.byref(h)), "ccmc_batch_create")
         self._h = h
 
-    def config(self, threads: int = 256, resident_max_sites: int = 1 << 18, ctas_per_sm: int = 2):
+    def config(self, threads: int = 256, resident_max_sites: int = 1 << 17, ctas_per_sm: int = 2):
         _check(lib().ccmc_batch_config(self._h, threads, resident_max_sites, ctas_per_sm),
                "ccmc_batch_config")
+
+    def autotune(self, probe_sweeps: int = 20):
+        """Time the candidate launch shapes on a probe batch of the same shapes
+        (cached per GPU and shape mix) and apply the fastest."""
+        from . import autotune
+
+        best = autotune.tune([(lat.Lx, lat.Ly) for lat in self.lattices], probe_sweeps)
+        self.config(*best)
+        return best
 
     def sweep(self, nsweeps, beta, Delta, V, J, obs_every: int = 0):
         n = len(self.lattices)
@@ -252,3 +293,78 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Server:
+    """Continuous-batching request loop (ccmc_server_*): independent simulations
+    admitted by a device-memory budget, advanced together in slices."""
+
+    def __init__(self, hbm_budget_bytes: int = 120 << 30, max_active: int = 1024,
+                 slice_ms: float = 20.0):
+        h = c_void_p()
+        _check(lib().ccmc_server_start(hbm_budget_bytes, max_active, slice_ms, ctypes.byref(h)),
+               "ccmc_server_start")
+        self._h = h
+        self._outs = {}
+
+    def submit(self, Lx, Ly, seed, n, nsweeps, beta, Delta, V, J, charged_frac=0.3,
+               obs_every=0, state_out: np.ndarray | None = None) -> int:
+        req = Request(Lx, Ly, seed & (2 ** 64 - 1), n, charged_frac, nsweeps, beta, Delta, V, J,
+                      obs_every, None)
+        if state_out is not None:
+            assert state_out.dtype == np.uint8 and state_out.size == Lx * Ly
+            assert state_out.flags.c_contiguous
+            req.state_out = state_out.ctypes.data
+        t = c_uint64()
+        _check(lib().ccmc_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)),
+               "ccmc_server_submit")
+        if state_out is not None:
+            self._outs[t.value] = state_out  # keep the buffer alive until the request is done
+        return t.value
+
+    def poll(self, ticket: int):
+        """Result dict once finished, None while pending."""
+        r = Result()
+        code = lib().ccmc_server_poll(self._h, ticket, ctypes.byref(r))
+        if code == PENDING:
+            return None
+        _check(code, "ccmc_server_poll")
+        self._outs.pop(ticket, None)
+        return r.as_dict()
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        r = Result()
+        _check(lib().ccmc_server_wait(self._h, ticket, ctypes.byref(r), timeout_s),
+               "ccmc_server_wait")
+        self._outs.pop(ticket, None)
+        return r.as_dict()
+
+    def series(self, ticket: int, cap: int = 1 << 16) -> np.ndarray:
+        buf = (Obs * cap)()
+        n = c_int64()
+        _check(lib().ccmc_server_series(self._h, ticket, buf, cap, ctypes.byref(n)),
+               "ccmc_server_series")
+        return np.frombuffer(buf, dtype=np.int64).reshape(cap, 9)[:n.value, :8].copy()
+
+    def release(self, ticket: int):
+        _check(lib().ccmc_server_release(self._h, ticket), "ccmc_server_release")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().ccmc_server_stats_get(self._h, ctypes.byref(st)), "ccmc_server_stats_get")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def stop(self):
+        if getattr(self, "_h", None):
+            lib().ccmc_server_stop(self._h)
+            self._h = None
+            self._outs.clear()
+
+    def __del__(self):
+        self.stop()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()

@@ -1,0 +1,95 @@
+"""Autotuner for batched sweeps: picks the launch shape of a batch by timing.
+
+The knobs (ccmc_batch_config) are the threads per CTA of the resident launch,
+its CTAs per SM, and the largest lattice kept in shared memory (the rest take
+the per-phase HBM/L2 path).  None of them changes results -- the random streams
+are keyed by (seed, phase, site) -- so the tuner may pick freely.
+
+A probe batch of synthetic lattices with the same shapes is swept for a few
+sweeps under every candidate; the fastest candidate is cached in a JSON file
+(paper_2301_11735_gb300/_build/autotune.json) keyed by the GPU name and the
+batch's shape signature.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+CANDIDATES = [
+    (threads, ctas, resident)
+    for threads in (128, 256)
+    for ctas in (2, 4)
+    for resident in (1 << 12, 1 << 17)
+] + [(64, 2, 1 << 17)]
+
+
+def _gpu_name() -> str:
+    try:
+        import torch
+
+        return torch.cuda.get_device_name()
+    except Exception:
+        return "cuda"
+
+
+def signature(shapes) -> str:
+    counts = {}
+    for s in shapes:
+        counts[tuple(s)] = counts.get(tuple(s), 0) + 1
+    key = ",".join(f"{a}x{b}:{n}" for (a, b), n in sorted(counts.items()))
+    return hashlib.sha1(key.encode()).hexdigest()[:16]
+
+
+def _load():
+    try:
+        with open(_CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(cache):
+    os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+    tmp = _CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, _CACHE)
+
+
+def tune(shapes, probe_sweeps: int = 20, params=(1.0, 0.0, 1.0, 1.0), use_cache: bool = True):
+    """Best (threads, ctas_per_sm, resident_max_sites) for a batch of `shapes`."""
+    import paper_2301_11735_gb300 as cc
+
+    key = f"{_gpu_name()}|{signature(shapes)}"
+    cache = _load() if use_cache else {}
+    if key in cache:
+        return tuple(cache[key]["config"])
+    lats = []
+    for i, (Lx, Ly) in enumerate(shapes):
+        lat = cc.Lattice(Lx, Ly)
+        lat.init_constrained(7919 + i, 0.1, 0.3)
+        lats.append(lat)
+    timings = {}
+    with cc.Batch(lats) as b:
+        for cand in CANDIDATES:
+            try:
+                b.config(*cand)
+            except cc.CcmcError:
+                continue
+            b.sweep(2, *params)  # warm-up
+            b.sync()
+            t0 = time.perf_counter()
+            b.sweep(probe_sweeps, *params)
+            b.sync()
+            timings[cand] = time.perf_counter() - t0
+    for lat in lats:
+        lat.close()
+    best = min(timings, key=timings.get)
+    cache[key] = {"config": list(best),
+                  "timings_ms": {str(list(c)): 1e3 * t for c, t in timings.items()}}
+    _store(cache)
+    return best

@@ -1,12 +1,13 @@
 """Build ``libccmc.so`` in-tree (``paper_2301_11735_gb300/_build``) for sm_103a.
 
-Four translation units are compiled in parallel and linked into one shared
+Five translation units are compiled in parallel and linked into one shared
 library that exports the C ABI of ``include/ccmc.h``:
 
 * ``csrc/ccmc_kernels.cu`` -- the CUDA kernels (nvcc, sm_103a only);
 * ``csrc/ccmc_api.cu``     -- host code of the C ABI (nvcc host pass);
 * ``csrc/ccmc_noalloc.cu`` -- the recount entry point that allocates nothing;
-* ``csrc/ccmc_tables.cpp`` -- FP64 threshold tables (g++).
+* ``csrc/ccmc_tables.cpp`` -- FP64 threshold tables (g++);
+* ``csrc/ccmc_server.cpp`` -- the continuous-batching server (g++, a host thread).
 
 All host code is compiled with ``-ffp-contract=off`` so the threshold tables
 round exactly as written (an FMA would change the last bit of some entries).
@@ -66,6 +67,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         "ccmc_tables.o": [os.environ.get("CXX", "g++"), "-c", "-std=c++17", "-O2", "-fPIC",
                           "-ffp-contract=off", f"-I{cuda}/include",
                           os.path.join(CSRC, "ccmc_tables.cpp")],
+        "ccmc_server.o": [os.environ.get("CXX", "g++"), "-c", "-std=c++17", "-O2", "-fPIC",
+                          "-pthread", f"-I{cuda}/include", os.path.join(CSRC, "ccmc_server.cpp")],
     }
     procs = []
     for obj, cmd in jobs.items():

@@ -489,6 +489,7 @@ int ccmc_set_state(ccmc_lattice *h, const uint8_t *host_in, uint64_t seed, int64
 // per-phase path on their own streams at the same time.
 struct ccmc_batch {
   std::vector<ccmc_lattice *> lats;
+  int cap = 0;  // largest number of lattices one launch may hold
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   JobDesc *d_jobs = nullptr;
@@ -519,6 +520,81 @@ JobDesc job_of(ccmc_lattice *h, int64_t nsweeps, int obs_every) {
 }
 }  // namespace
 
+namespace ccmc {
+
+int batch_run(ccmc_batch *b, const std::vector<ccmc_lattice *> &lats, const int64_t *nsweeps,
+              const double *beta, const double *Delta, const double *V, const double *J,
+              const int *obs_every) {
+  const int n = (int)lats.size();
+  if (n > b->cap) return CCMC_E_INVAL;
+  for (int i = 0; i < n; ++i) {
+    if (nsweeps[i] < 0 || !(beta[i] >= 0.0) || !std::isfinite(Delta[i]) ||
+        !std::isfinite(V[i]) || !std::isfinite(J[i]))
+      return CCMC_E_INVAL;
+    ccmc_lattice *h = lats[i];
+    if (!h || !h->initialised || h->phases_done % 8) return CCMC_E_STATE;
+    for (int k = 0; k < i; ++k)
+      if (lats[k] == h) return CCMC_E_INVAL;  // a lattice may appear once
+  }
+  std::vector<JobDesc> jobs;
+  std::vector<int> resident;
+  for (int i = 0; i < n; ++i) {
+    ccmc_lattice *h = lats[i];
+    const int64_t sites = 16 * h->g.cstride * 16;  // padded sites held in words
+    if (nsweeps[i] == 0 || sites > b->resident_max_sites) continue;
+    // order the batch stream after work already queued on this lattice's stream
+    if (h->stream != b->stream) {
+      CK(cudaEventRecord(b->lat_ev[i], h->stream));
+      CK(cudaStreamWaitEvent(b->stream, b->lat_ev[i], 0));
+    }
+    int rc = upload_params_on(h, beta[i], Delta[i], V[i], J[i], b->stream);
+    if (rc) return rc;
+    jobs.push_back(job_of(h, nsweeps[i], obs_every[i]));
+    resident.push_back(i);
+  }
+  if (!jobs.empty()) {
+    // largest first: the queue hands the longest jobs out before the short ones
+    std::vector<int> order(jobs.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+      const int64_t wx = (int64_t)jobs[x].g.Lx * jobs[x].g.Ly * jobs[x].nsweeps;
+      const int64_t wy = (int64_t)jobs[y].g.Lx * jobs[y].g.Ly * jobs[y].nsweeps;
+      return wx > wy;
+    });
+    std::vector<JobDesc> sorted;
+    int64_t max_words = 0;
+    for (int k : order) {
+      sorted.push_back(jobs[k]);
+      const int64_t w = 16 * jobs[k].g.cstride;
+      if (w > max_words) max_words = w;
+    }
+    CK(cudaMemcpyAsync(b->d_jobs, sorted.data(), sizeof(JobDesc) * sorted.size(),
+                       cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream));
+    int grid = b->sms * b->ctas_per_sm;
+    if (grid > (int)sorted.size()) grid = (int)sorted.size();
+    CK(launch_resident(b->d_jobs, (int)sorted.size(), b->d_queue, grid, b->threads, max_words,
+                       b->stream));
+    CK(cudaEventRecord(b->ev, b->stream));
+    for (int i : resident) {
+      ccmc_lattice *h = lats[i];
+      h->phases_done += 8 * nsweeps[i];
+      if (h->stream != b->stream) CK(cudaStreamWaitEvent(h->stream, b->ev, 0));
+    }
+  }
+  // the rest on their own streams, overlapping the resident launch
+  for (int i = 0; i < n; ++i) {
+    ccmc_lattice *h = lats[i];
+    const int64_t sites = 16 * h->g.cstride * 16;
+    if (nsweeps[i] == 0 || sites <= b->resident_max_sites) continue;
+    const int rc = ccmc_sweep(h, nsweeps[i], beta[i], Delta[i], V[i], J[i], obs_every[i]);
+    if (rc) return rc;
+  }
+  return CCMC_OK;
+}
+
+}  // namespace ccmc
+
 extern "C" {
 
 int ccmc_batch_create(int count, ccmc_lattice *const *lattices, void *cuda_stream,
@@ -527,9 +603,22 @@ int ccmc_batch_create(int count, ccmc_lattice *const *lattices, void *cuda_strea
   *out = nullptr;
   for (int i = 0; i < count; ++i)
     if (!lattices[i]) return CCMC_E_INVAL;
+  const int rc = ccmc::batch_new(count, (cudaStream_t)cuda_stream, out);
+  if (rc != CCMC_OK) return rc;
+  (*out)->lats.assign(lattices, lattices + count);
+  return CCMC_OK;
+}
+
+}  // extern "C"
+
+int ccmc::batch_new(int cap, cudaStream_t stream, ccmc_batch **out) {
+  if (!out || cap < 1) return CCMC_E_INVAL;
+  *out = nullptr;
   ccmc_batch *b = new (std::nothrow) ccmc_batch();
   if (!b) return CCMC_E_NOMEM;
-  b->lats.assign(lattices, lattices + count);
+  b->cap = cap;
+  const int count = cap;
+  void *cuda_stream = (void *)stream;
   auto fail = [&](int code) {
     ccmc_batch_destroy(b);
     return code;
@@ -560,6 +649,8 @@ int ccmc_batch_create(int count, ccmc_lattice *const *lattices, void *cuda_strea
   *out = b;
   return CCMC_OK;
 }
+
+extern "C" {
 
 int ccmc_batch_destroy(ccmc_batch *b) {
   if (!b) return CCMC_E_INVAL;
@@ -594,71 +685,8 @@ int ccmc_batch_config(ccmc_batch *b, int resident_threads, int64_t resident_max_
 int ccmc_batch_sweep(ccmc_batch *b, const int64_t *nsweeps, const double *beta,
                      const double *Delta, const double *V, const double *J, int obs_every) {
   if (!b || !nsweeps || !beta || !Delta || !V || !J) return CCMC_E_INVAL;
-  const int n = (int)b->lats.size();
-  for (int i = 0; i < n; ++i) {
-    if (nsweeps[i] < 0 || !(beta[i] >= 0.0) || !std::isfinite(Delta[i]) ||
-        !std::isfinite(V[i]) || !std::isfinite(J[i]))
-      return CCMC_E_INVAL;
-    ccmc_lattice *h = b->lats[i];
-    if (!h->initialised || h->phases_done % 8) return CCMC_E_STATE;
-    for (int k = 0; k < i; ++k)
-      if (b->lats[k] == h) return CCMC_E_INVAL;  // a lattice may appear once
-  }
-  std::vector<JobDesc> jobs;
-  std::vector<int> resident;
-  for (int i = 0; i < n; ++i) {
-    ccmc_lattice *h = b->lats[i];
-    const int64_t sites = 16 * h->g.cstride * 16;  // padded sites held in words
-    if (nsweeps[i] == 0 || sites > b->resident_max_sites) continue;
-    // order the batch stream after work already queued on this lattice's stream
-    if (h->stream != b->stream) {
-      CK(cudaEventRecord(b->lat_ev[i], h->stream));
-      CK(cudaStreamWaitEvent(b->stream, b->lat_ev[i], 0));
-    }
-    int rc = upload_params_on(h, beta[i], Delta[i], V[i], J[i], b->stream);
-    if (rc) return rc;
-    jobs.push_back(job_of(h, nsweeps[i], obs_every));
-    resident.push_back(i);
-  }
-  if (!jobs.empty()) {
-    // largest first: the queue hands the longest jobs out before the short ones
-    std::vector<int> order(jobs.size());
-    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
-    std::sort(order.begin(), order.end(), [&](int x, int y) {
-      const int64_t wx = (int64_t)jobs[x].g.Lx * jobs[x].g.Ly * jobs[x].nsweeps;
-      const int64_t wy = (int64_t)jobs[y].g.Lx * jobs[y].g.Ly * jobs[y].nsweeps;
-      return wx > wy;
-    });
-    std::vector<JobDesc> sorted;
-    int64_t max_words = 0;
-    for (int k : order) {
-      sorted.push_back(jobs[k]);
-      const int64_t w = 16 * jobs[k].g.cstride;
-      if (w > max_words) max_words = w;
-    }
-    CK(cudaMemcpyAsync(b->d_jobs, sorted.data(), sizeof(JobDesc) * sorted.size(),
-                       cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream));
-    int grid = b->sms * b->ctas_per_sm;
-    if (grid > (int)sorted.size()) grid = (int)sorted.size();
-    CK(launch_resident(b->d_jobs, (int)sorted.size(), b->d_queue, grid, b->threads, max_words,
-                       b->stream));
-    CK(cudaEventRecord(b->ev, b->stream));
-    for (int i : resident) {
-      ccmc_lattice *h = b->lats[i];
-      h->phases_done += 8 * nsweeps[i];
-      if (h->stream != b->stream) CK(cudaStreamWaitEvent(h->stream, b->ev, 0));
-    }
-  }
-  // the rest on their own streams, overlapping the resident launch
-  for (int i = 0; i < n; ++i) {
-    ccmc_lattice *h = b->lats[i];
-    const int64_t sites = 16 * h->g.cstride * 16;
-    if (nsweeps[i] == 0 || sites <= b->resident_max_sites) continue;
-    const int rc = ccmc_sweep(h, nsweeps[i], beta[i], Delta[i], V[i], J[i], obs_every);
-    if (rc) return rc;
-  }
-  return CCMC_OK;
+  std::vector<int> every(b->lats.size(), obs_every);
+  return ccmc::batch_run(b, b->lats, nsweeps, beta, Delta, V, J, every.data());
 }
 
 int ccmc_batch_sync(ccmc_batch *b) {

@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
+
+struct ccmc_lattice;
+struct ccmc_batch;
 
 namespace ccmc {
 
@@ -97,5 +101,14 @@ cudaError_t launch_resident(const JobDesc *d_jobs, int njobs, int *d_queue, int 
 int64_t resident_smem_bytes(int64_t max_words);
 cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                           uint32_t k1, int64_t count, uint32_t *out, cudaStream_t s);
+
+// A batch with no fixed members, room for `cap` lattices, on `stream`.
+int batch_new(int cap, cudaStream_t stream, ccmc_batch **out);
+
+// Sweep a list of lattices (at most the batch's capacity) with per-lattice
+// sweeps, parameters and observable intervals through the batch machinery.
+int batch_run(ccmc_batch *b, const std::vector<ccmc_lattice *> &lats, const int64_t *nsweeps,
+              const double *beta, const double *Delta, const double *V, const double *J,
+              const int *obs_every);
 
 }  // namespace ccmc
