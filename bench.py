@@ -14,6 +14,12 @@ timed region.  `e2e` repeats the steps through the C ABI with host buffers:
 every step uploads the four lattices from pinned host memory (ccmc_set_state)
 and reads the observable records back (ccmc_obs_series).
 
+Beside the headline the same JSON line carries two more measurements of the
+spec patterns: `batched` (512 replicas of uneven L in one persistent
+launch, against back-to-back single-lattice launches) and `served` (a Poisson
+request stream through the continuous-batching server: p50/p99 latency,
+achieved vs offered site-updates/s, against back-to-back plain runs).
+
 `--impl reference` times the CPU oracle (single-threaded C) on a bounded sample
 of the same workload.  Under torchrun each rank runs its own four lattices
 (weak scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -166,6 +172,96 @@ def cpu_baseline_sample(target_s: float = 12.0):
             "sample": f"{n} sweeps of the 4096^2 lattice at T={s.T} ({dt:.1f} s, 1 thread)"}
 
 
+def measure_batched(cc, nsweeps=5000, plain_sample=32, plain_sweeps=200):
+    """512 independent replicas (L in {32..256}, 5000 sweeps) in one batched
+    launch, against the same lattices swept back to back one at a time."""
+    import torch
+
+    from workloads import replicas_512
+
+    sims = replicas_512(nsweeps=nsweeps)
+    lats = []
+    for s in sims:
+        lat = cc.Lattice(s.Lx, s.Ly)
+        lat.init_constrained(s.seed, s.n, s.charged_frac)
+        lats.append(lat)
+    cols = ([s.beta for s in sims], [s.Delta for s in sims], [s.V for s in sims],
+            [s.J for s in sims])
+    with cc.Batch(lats) as b:
+        cfg = b.autotune(probe_sweeps=10)
+        b.sweep(3, *cols)
+        b.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.sweep(nsweeps, *cols)
+        b.sync()
+        dt = time.perf_counter() - t0
+    work = sum(s.sites for s in sims) * nsweeps
+    sub = list(zip(sims, lats))[:plain_sample]
+    t0 = time.perf_counter()
+    for s, lat in sub:
+        lat.sweep(plain_sweeps, s.beta, s.Delta, s.V, s.J)
+        lat.sync()
+    dt_plain = time.perf_counter() - t0
+    plain = sum(s.sites for s, _ in sub) * plain_sweeps / dt_plain
+    for lat in lats:
+        lat.close()
+    return {"workload": "512 replicas, L~U{32,64,128,256}, T grid [0.1,3], n~U{0,.1,.2,.3}, "
+                        "Delta~U{-.5,0,.5}, V=J=1, 5000 sweeps",
+            "value": work / dt, "unit": "site-updates/s", "seconds": dt,
+            "config": {"threads": cfg[0], "ctas_per_sm": cfg[1], "resident_max_sites": cfg[2]},
+            "plain_back_to_back": {"value": plain, "unit": "site-updates/s",
+                                   "sample": f"{plain_sample} of the lattices, {plain_sweeps} "
+                                             "sweeps each, one ccmc_sweep call at a time"},
+            "speedup_vs_plain": (work / dt) / plain}
+
+
+def measure_served(cc, count=120, plain_sample=24):
+    """Poisson request stream (200 req/s; L log-uniform in [32, 2048]; sweeps
+    log-uniform in [1e3, 1e5]) through the continuous-batching server under a
+    120 GB budget; p50/p99 latency from submission to completion."""
+    import numpy as np
+
+    from workloads import request_stream
+
+    arrivals, sims = request_stream(count=count)
+    srv = cc.Server(hbm_budget_bytes=120 << 30, max_active=1024, slice_ms=20.0)
+    t0 = time.perf_counter()
+    tickets = []
+    for a, s in zip(arrivals, sims):
+        delay = a - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(s.Lx, s.Ly, s.seed, s.n, s.nsweeps, s.beta, s.Delta, s.V, s.J))
+    res = [srv.wait(t, timeout_s=3600.0) for t in tickets]
+    stats = srv.stats()
+    srv.stop()
+    lat = np.array([r["done_s"] - r["submit_s"] for r in res])
+    work = sum(r["site_updates"] for r in res)
+    span = max(r["done_s"] for r in res) - min(r["submit_s"] for r in res)
+    offered = sum(s.sites * s.nsweeps for s in sims) / max(arrivals[-1], 1e-9)
+    sub = sims[:plain_sample]
+    cap = 2000  # a lone small lattice is launch-bound: bound the sample's run time
+    tp = time.perf_counter()
+    for s in sub:
+        with cc.Lattice(s.Lx, s.Ly) as one:
+            one.init_constrained(s.seed, s.n, s.charged_frac)
+            one.sweep(min(s.nsweeps, cap), s.beta, s.Delta, s.V, s.J)
+            one.observables()
+    plain = sum(s.sites * min(s.nsweeps, cap) for s in sub) / (time.perf_counter() - tp)
+    return {"workload": f"{count} Poisson requests at 200/s (L log-U[32,2048], sweeps "
+                        "log-U[1e3,1e5], T~U[0.1,3], n~U[0,.4], Delta~U[-1,1], V~U[0,2], J=1), "
+                        "120 GB budget",
+            "value": work / span, "unit": "site-updates/s", "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "offered": offered,
+            "completed": stats["completed"], "slices": stats["slices"],
+            "plain_back_to_back": {"value": plain, "unit": "site-updates/s",
+                                   "sample": f"first {plain_sample} requests one at a time "
+                                             f"(init, ccmc_sweep, observables), at most {cap} "
+                                             "sweeps each"},
+            "speedup_vs_plain": (work / span) / plain}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -290,6 +386,9 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(sum(h.numel() for h in host_states)),
                     "d2h_bytes_per_step": int(rec_bytes)},
         }
+        if not args.no_side:
+            line["batched"] = measure_batched(cc)
+            line["served"] = measure_served(cc)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(line), flush=True)
@@ -306,6 +405,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the batched-replica and served-stream measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
