@@ -209,7 +209,7 @@ def measure_batched(cc, nsweeps=5000, plain_sample=32, plain_sweeps=200):
     return {"workload": "512 replicas, L~U{32,64,128,256}, T grid [0.1,3], n~U{0,.1,.2,.3}, "
                         "Delta~U{-.5,0,.5}, V=J=1, 5000 sweeps",
             "value": work / dt, "unit": "site-updates/s", "seconds": dt,
-            "config": {"threads": cfg[0], "ctas_per_sm": cfg[1], "resident_max_sites": cfg[2]},
+            "config": {"threads": cfg[0], "resident_max_sites": cfg[1], "ctas_per_sm": cfg[2]},
             "plain_back_to_back": {"value": plain, "unit": "site-updates/s",
                                    "sample": f"{plain_sample} of the lattices, {plain_sweeps} "
                                              "sweeps each, one ccmc_sweep call at a time"},

@@ -19,12 +19,15 @@ import time
 
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
+# (threads per CTA, largest resident lattice in sites, CTAs per SM): the
+# argument order of Batch.config
+DEFAULT = (256, 1 << 17, 2)
 CANDIDATES = [
-    (threads, ctas, resident)
+    (threads, resident, ctas)
     for threads in (128, 256)
-    for ctas in (2, 4)
     for resident in (1 << 12, 1 << 17)
-] + [(64, 2, 1 << 17)]
+    for ctas in (2, 4)
+] + [(64, 1 << 17, 2)]
 
 
 def _gpu_name() -> str:
@@ -61,7 +64,7 @@ def _store(cache):
 
 
 def tune(shapes, probe_sweeps: int = 20, params=(1.0, 0.0, 1.0, 1.0), use_cache: bool = True):
-    """Best (threads, ctas_per_sm, resident_max_sites) for a batch of `shapes`."""
+    """Best (threads, resident_max_sites, ctas_per_sm) for a batch of `shapes`."""
     import paper_2301_11735_gb300 as cc
 
     key = f"{_gpu_name()}|{signature(shapes)}"
@@ -88,6 +91,8 @@ def tune(shapes, probe_sweeps: int = 20, params=(1.0, 0.0, 1.0, 1.0), use_cache:
             timings[cand] = time.perf_counter() - t0
     for lat in lats:
         lat.close()
+    if not timings:
+        return DEFAULT
     best = min(timings, key=timings.get)
     cache[key] = {"config": list(best),
                   "timings_ms": {str(list(c)): 1e3 * t for c, t in timings.items()}}

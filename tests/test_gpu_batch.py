@@ -137,3 +137,18 @@ def test_batch_rejects_bad_use(cc):
             b.config(100, 1 << 16, 2)
     a.close()
     b_.close()
+
+
+def test_autotuner_picks_a_valid_shape_and_results_stay_exact(cc, tmp_path, monkeypatch):
+    from paper_2301_11735_gb300 import autotune
+
+    monkeypatch.setattr(autotune, "_CACHE", str(tmp_path / "tune.json"))
+    shapes = MIX[:6]
+    best = autotune.tune(shapes, probe_sweeps=3)
+    assert best in autotune.CANDIDATES
+    assert autotune.tune(shapes, probe_sweeps=3) == best  # cached
+    nsw = [6] * len(shapes)
+    got = _run_batch(cc, shapes, nsw, obs_every=2, cfg=best)
+    ref = _run_single(cc, shapes, nsw, obs_every=2)
+    for (s1, r1), (s2, r2) in zip(got, ref):
+        assert np.array_equal(s1, s2) and np.array_equal(r1, r2)
