@@ -3,12 +3,12 @@
 Workload (default): the 4096^2 temperature sweep -- four lattices of 4096 x 4096
 sites (Delta = 0, V = 0.5, J = 1, n = 0.1, charged fraction 0.3) at
 T = 0.2, 0.5, 1.0, 2.0, seeds 20..23.  One step = 10 sweeps of each of the
-four lattices, the four running concurrently on their own streams, plus the
-observable recount that closes every 10-sweep interval.  The metric is
+four lattices (one ccmc_batch call; the four run concurrently on their own
+streams), plus the observable recount that closes every 10-sweep interval.  The metric is
 site-updates per second (one sweep = N site-updates).
 
 Timing: W warm-up steps, then K timed steps, each bracketed by CUDA events on
-the issuing stream (the other streams join it); L2 is flushed (a 256 MB write)
+the issuing stream; L2 is flushed (a 256 MB write)
 between timed steps, outside the events.  nvidia-smi samples clocks during the
 timed region.  `e2e` repeats the steps through the C ABI with host buffers:
 every step uploads the four lattices from pinned host memory (ccmc_set_state)
@@ -278,11 +278,17 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     sims = temperature_sweep_4096(obs_every=STEP_SWEEPS)
     sims = [type(s)(**{**s.__dict__, "seed": s.seed + 4 * rank}) for s in sims]
+    # explicit streams: one issuing stream for the timing events and the L2 flush,
+    # one per lattice so that the four run concurrently (torch's default stream
+    # has handle 0, which the library reads as "create your own")
+    main = torch.cuda.Stream()
     streams = [torch.cuda.Stream() for _ in sims]
-    main = torch.cuda.current_stream()
     lats = [cc.Lattice(s.Lx, s.Ly, stream=st) for s, st in zip(sims, streams)]
     for lat, s in zip(lats, sims):
         lat.init_constrained(s.seed, s.n, s.charged_frac)
+    batch = cc.Batch(lats, stream=main)
+    cols = ([s.beta for s in sims], [s.Delta for s in sims], [s.V for s in sims],
+            [s.J for s in sims])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
 
     def step():
@@ -291,8 +297,7 @@ def run_ours(args):
         ev0.record(main)
         for st in streams:
             st.wait_event(ev0)
-        for lat, s in zip(lats, sims):
-            lat.sweep(STEP_SWEEPS, s.beta, s.Delta, s.V, s.J, obs_every=s.obs_every)
+        batch.sweep(STEP_SWEEPS, *cols, obs_every=STEP_SWEEPS)
         for st in streams:
             e = torch.cuda.Event()
             e.record(st)
@@ -311,7 +316,8 @@ def run_ours(args):
     t_wall = time.perf_counter()
     with sampler:
         for _ in range(args.steps):
-            flush.zero_()
+            with torch.cuda.stream(main):
+                flush.zero_()
             evs.append(step())
         torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
@@ -325,23 +331,23 @@ def run_ours(args):
     updates_per_step = sum(s.sites for s in sims) * STEP_SWEEPS
     value = updates_per_step * args.steps * world / total_s
 
-    # dominant kernel: one colour phase of one 4096^2 lattice, timed launch by
-    # launch with events on its own stream (the kernel the steps are made of)
-    lat, s = lats[0], sims[0]
-    st = streams[0]
-    n_cal = 64
+    # dominant kernel: the colour phase of one 4096^2 lattice.  A chunk of 16
+    # sweeps is 128 phase launches (plus a one-thread counter advance), replayed
+    # as one graph; events on the lattice's stream around it give the average
+    # phase-launch time (slightly over, by the advance).
+    lat0, s0, st0 = lats[0], sims[0], streams[0]
     cal = []
-    with torch.cuda.stream(st):
-        for _ in range(n_cal):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(st)
-            lat.phases(1, s.beta, s.Delta, s.V, s.J)
-            b.record(st)
-            cal.append((a, b))
+    for _ in range(6):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st0)
+        lat0.sweep(16, s0.beta, s0.Delta, s0.V, s0.J, obs_every=0)
+        b.record(st0)
+        cal.append((a, b))
     torch.cuda.synchronize()
-    phase_ms = statistics.mean(x.elapsed_time(y) for x, y in cal[8:])
-    alg_bytes = 1.5 * s.sites / 8  # 1.5 B per site-update, N/8 updates per phase
+    phase_ms = statistics.mean(x.elapsed_time(y) for x, y in cal[2:]) / 128
+    # 1.5 B per site-update, N/8 updates per phase
+    alg_bytes = 1.5 * s0.sites / 8
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (phase_ms * 1e-3) / 1e9
 
@@ -357,8 +363,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for lat, s, h in zip(lats, sims, host_states):
             lat.set_state_ptr(h.data_ptr(), s.seed, 0)
-        for lat, s in zip(lats, sims):
-            lat.sweep(STEP_SWEEPS, s.beta, s.Delta, s.V, s.J, obs_every=s.obs_every)
+        batch.sweep(STEP_SWEEPS, *cols, obs_every=STEP_SWEEPS)
         recs = [lat.obs_series(cap=4) for lat in lats]
         dt = time.perf_counter() - t0
         rec_bytes = sum(r.nbytes for r in recs)
@@ -377,10 +382,11 @@ def run_ours(args):
                        "lattices_per_gpu": len(sims), "sweeps_per_step": STEP_SWEEPS,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
             "clocks": clocks, "wall_s": t_wall,
+            # per step and lattice: 80 phase launches, a recount, a counter advance
             "gpu_launches": args.steps * len(sims) * (STEP_SWEEPS * 8 + 2),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "phase_kernel (one colour phase, 4096^2)",
+                         "kernel": "phase_kernel (one colour phase of a 4096^2 lattice)",
                          "peak_source": peak_kind, "launch_ms": phase_ms},
             "e2e": {"value": e2e_value, "unit": "site-updates/s",
                     "h2d_bytes_per_step": int(sum(h.numel() for h in host_states)),
@@ -392,6 +398,7 @@ def run_ours(args):
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(line), flush=True)
+    batch.close()
     for lat in lats:
         lat.close()
     if dist:

@@ -33,6 +33,7 @@ struct GraphEntry {
 };
 
 constexpr int kChunk = 16;
+constexpr int kLockstepMin = 8;  // lattices per lock-step group
 
 }  // namespace
 
@@ -88,12 +89,13 @@ int upload_params_on(ccmc_lattice *h, double beta, double Delta, double V, doubl
       h->params[3] == J)
     return CCMC_OK;
   std::vector<uint32_t> thr32(kTableN);
-  std::vector<uint16_t> thr16(kThr16Bytes / 2, 0);
+  std::vector<uint32_t> thrhi(kThrHiWords, 0);
   build_thresholds(beta, Delta, V, J, thr32.data());
-  for (int i = 0; i < kTableN; ++i) thr16[i] = (uint16_t)(thr32[i] >> 16);
+  for (int i = 0; i < kTableN; ++i) thrhi[i] = thr32[i] & 0xFFFF0000u;
   CK(cudaMemcpyAsync(h->t.thr32, thr32.data(), sizeof(uint32_t) * kTableN,
                      cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(h->t.thr16, thr16.data(), kThr16Bytes, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->t.thrhi, thrhi.data(), sizeof(uint32_t) * kThrHiWords,
+                     cudaMemcpyHostToDevice, st));
   // pageable sources: the copies are staged before the calls return
   h->have_params = true;
   h->params[0] = beta;
@@ -143,6 +145,40 @@ int run_graph(ccmc_lattice *h, int sweeps, int obs_every) {
     hit = &h->graphs.back();
   }
   CK(cudaGraphLaunch(hit->exec, h->stream));
+  return CCMC_OK;
+}
+
+// Drives nsweeps sweeps from absolute sweep index sweeps_done: replayable
+// chunks of G sweeps (chunk(G, obs): G a multiple of obs when 0 < obs <= 16,
+// started aligned to obs) where possible, single directly launched sweeps
+// (single(obs_due)) to align or finish.
+template <typename Chunk, typename Single>
+int drive_sweeps(int64_t sweeps_done, int64_t nsweeps, int obs_every, Chunk chunk, Single single) {
+  int64_t s = 0;
+  while (s < nsweeps) {
+    const int64_t abs_sweep = sweeps_done + s;
+    const int64_t remaining = nsweeps - s;
+    if (obs_every > 0 && obs_every <= kChunk) {
+      const int g = obs_every * (kChunk / obs_every);
+      if (abs_sweep % obs_every == 0 && remaining >= g) {
+        const int rc = chunk(g, obs_every);
+        if (rc) return rc;
+        s += g;
+        continue;
+      }
+    } else {
+      const int64_t dist = obs_every > 0 ? obs_every - abs_sweep % obs_every : INT64_MAX;
+      if (remaining >= kChunk && dist > kChunk) {
+        const int rc = chunk(kChunk, 0);
+        if (rc) return rc;
+        s += kChunk;
+        continue;
+      }
+    }
+    const int rc = single(obs_every > 0 && (abs_sweep + 1) % obs_every == 0);
+    if (rc) return rc;
+    s += 1;
+  }
   return CCMC_OK;
 }
 
@@ -216,6 +252,7 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   g.cstride = (int64_t)g.Cy * g.W;
   const uint64_t N = (uint64_t)Lx * (uint64_t)Ly;
   g.rej = (0 - N) % N;
+  h->cfg.phase_grid_cap = phase_resident_grid((g.Cx & 15) == 0);
   while (((int64_t)1 << (2 * h->h)) < (int64_t)N) ++h->h;
   h->ring_cap = obs_capacity > 0 ? obs_capacity : 4096;
   cudaGetDevice(&h->device);
@@ -237,7 +274,7 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
       cudaMalloc(&h->d_ring, sizeof(int64_t) * 8 * h->ring_cap) != cudaSuccess ||
       cudaMalloc(&h->d_flag, sizeof(int)) != cudaSuccess)
     return fail(CCMC_E_NOMEM);
-  const size_t tb = sizeof(uint32_t) * kTableN + 2 * sizeof(uint32_t) * 2 * kTransN + kThr16Bytes;
+  const size_t tb = sizeof(uint32_t) * (kTableN + 4 * kTransN + kThrHiWords);
   if (cudaMalloc(&h->d_tables, tb) != cudaSuccess) return fail(CCMC_E_NOMEM);
   char *p = (char *)h->d_tables;
   h->t.thr32 = (uint32_t *)p;
@@ -246,7 +283,7 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   p += sizeof(uint32_t) * 2 * kTransN;
   h->t.trans_near = (uint32_t *)p;
   p += sizeof(uint32_t) * 2 * kTransN;
-  h->t.thr16 = (uint16_t *)p;
+  h->t.thrhi = (uint32_t *)p;
   g.words = h->d_words;
   g.ctl = h->d_ctl;
   uint32_t tf[2 * kTransN], tn[2 * kTransN];
@@ -328,36 +365,18 @@ int ccmc_sweep(ccmc_lattice *h, int64_t nsweeps, double beta, double Delta, doub
                         h->stream));
     --nsweeps;
   }
-  const int64_t sweeps_done = h->phases_done / 8;
-  int64_t s = 0;
-  while (s < nsweeps) {
-    const int64_t abs_sweep = sweeps_done + s;
-    const int64_t remaining = nsweeps - s;
-    if (obs_every > 0 && obs_every <= kChunk) {
-      const int g = obs_every * (kChunk / obs_every);
-      if (abs_sweep % obs_every == 0 && remaining >= g) {
-        rc = run_graph(h, g, obs_every);
-        if (rc) return rc;
-        s += g;
-        continue;
-      }
-    } else {
-      const int64_t dist = obs_every > 0 ? obs_every - abs_sweep % obs_every : INT64_MAX;
-      if (remaining >= kChunk && dist > kChunk) {
-        rc = run_graph(h, kChunk, 0);
-        if (rc) return rc;
-        s += kChunk;
-        continue;
-      }
-    }
-    // one sweep, launched directly
-    for (int p = 0; p < 8; ++p) CK(launch_phase(h->g, h->t, p, h->cfg, h->stream));
-    if (obs_every > 0 && (abs_sweep + 1) % obs_every == 0)
-      CK(launch_recount(h->g, h->d_partials, h->d_ring, h->ring_cap, h->d_hist, h->nbins, 1,
-                        h->stream));
-    CK(launch_advance(h->d_ctl, 8, h->stream));
-    s += 1;
-  }
+  rc = drive_sweeps(
+      h->phases_done / 8, nsweeps, obs_every,
+      [&](int g, int obs) { return run_graph(h, g, obs); },
+      [&](bool obs_due) {
+        for (int p = 0; p < 8; ++p) CK(launch_phase(h->g, h->t, p, h->cfg, h->stream));
+        if (obs_due)
+          CK(launch_recount(h->g, h->d_partials, h->d_ring, h->ring_cap, h->d_hist, h->nbins, 1,
+                            h->stream));
+        CK(launch_advance(h->d_ctl, 8, h->stream));
+        return CCMC_OK;
+      });
+  if (rc) return rc;
   h->phases_done += 8 * nsweeps;
   return CCMC_OK;
 }
@@ -500,13 +519,21 @@ struct ccmc_batch {
   int sms = 152;
   cudaEvent_t ev = nullptr;
   std::vector<cudaEvent_t> lat_ev;
+  MultiJob *d_multi = nullptr;  // lock-step groups of large lattices
+  struct MultiGraph {
+    std::vector<ccmc_lattice *> members;
+    int sweeps, obs_every;
+    int64_t off;
+    cudaGraphExec_t exec;
+  };
+  std::vector<MultiGraph> graphs;
 };
 
 namespace {
 JobDesc job_of(ccmc_lattice *h, int64_t nsweeps, int obs_every) {
   JobDesc d{};
   d.g = h->g;
-  d.thr16 = reinterpret_cast<const uint32_t *>(h->t.thr16);
+  d.thrhi = h->t.thrhi;
   d.thr32 = h->t.thr32;
   d.trans_far = h->t.trans_far;
   d.trans_near = h->t.trans_near;
@@ -520,11 +547,106 @@ JobDesc job_of(ccmc_lattice *h, int64_t nsweeps, int obs_every) {
 }
 }  // namespace
 
+namespace {
+
+struct MultiGroup {
+  std::vector<ccmc_lattice *> m;
+  int64_t off;  // first slot in d_multi
+  int grid;
+  bool aligned;
+};
+
+int enqueue_multi_chunk(ccmc_batch *b, const MultiGroup &G, int sweeps, int obs_every) {
+  for (int s = 0; s < sweeps; ++s) {
+    for (int p = 0; p < 8; ++p)
+      CK(launch_phase_multi(b->d_multi + G.off, (int)G.m.size(), G.grid, G.aligned, 8LL * s + p,
+                            b->stream));
+    if (obs_every > 0 && (s + 1) % obs_every == 0)
+      for (ccmc_lattice *h : G.m)
+        CK(launch_recount(h->g, h->d_partials, h->d_ring, h->ring_cap, h->d_hist, h->nbins,
+                          s + 1, b->stream));
+  }
+  for (ccmc_lattice *h : G.m) CK(launch_advance(h->d_ctl, 8LL * sweeps, b->stream));
+  return CCMC_OK;
+}
+
+int run_multi_graph(ccmc_batch *b, const MultiGroup &G, int sweeps, int obs_every) {
+  for (auto &e : b->graphs)
+    if (e.members == G.m && e.sweeps == sweeps && e.obs_every == obs_every && e.off == G.off) {
+      CK(cudaGraphLaunch(e.exec, b->stream));
+      return CCMC_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = enqueue_multi_chunk(b, G, sweeps, obs_every);
+  const cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+  if (rc != CCMC_OK || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return CCMC_E_CUDA;
+  }
+  ccmc_batch::MultiGraph e{G.m, sweeps, obs_every, G.off, nullptr};
+  const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return CCMC_E_CUDA;
+  b->graphs.push_back(e);
+  CK(cudaGraphLaunch(e.exec, b->stream));
+  return CCMC_OK;
+}
+
+// Sweep a lock-step group (same position, sweeps, observable interval and
+// alignment) with one phase launch per phase for all of them.
+int run_multi(ccmc_batch *b, MultiGroup &G, int64_t nsweeps, int obs_every) {
+  int64_t words = 0;
+  for (ccmc_lattice *h : G.m) words += (int64_t)h->g.Cy * h->g.W;
+  const int wave = phase_resident_grid(G.aligned);
+  std::vector<MultiJob> jobs;
+  int begin = 0;
+  for (ccmc_lattice *h : G.m) {
+    const int64_t w = (int64_t)h->g.Cy * h->g.W;
+    int share = (int)((double)wave * (double)w / (double)words);
+    const int64_t need = (w + 255) / 256;  // more CTAs than a word each would idle
+    if (share > need) share = (int)need;
+    if (share < 1) share = 1;
+    MultiJob j{};
+    j.g = h->g;
+    j.thrhi = h->t.thrhi;
+    j.thr32 = h->t.thr32;
+    j.trans_far = h->t.trans_far;
+    j.trans_near = h->t.trans_near;
+    j.cta_begin = begin;
+    j.cta_count = share;
+    begin += share;
+    jobs.push_back(j);
+  }
+  G.grid = begin;
+  CK(cudaMemcpyAsync(b->d_multi + G.off, jobs.data(), sizeof(MultiJob) * jobs.size(),
+                     cudaMemcpyHostToDevice, b->stream));
+  const int rc = drive_sweeps(
+      G.m[0]->phases_done / 8, nsweeps, obs_every,
+      [&](int g, int obs) { return run_multi_graph(b, G, g, obs); },
+      [&](bool obs_due) {
+        for (int p = 0; p < 8; ++p)
+          CK(launch_phase_multi(b->d_multi + G.off, (int)G.m.size(), G.grid, G.aligned, p,
+                                b->stream));
+        if (obs_due)
+          for (ccmc_lattice *h : G.m)
+            CK(launch_recount(h->g, h->d_partials, h->d_ring, h->ring_cap, h->d_hist, h->nbins,
+                              1, b->stream));
+        for (ccmc_lattice *h : G.m) CK(launch_advance(h->d_ctl, 8, b->stream));
+        return CCMC_OK;
+      });
+  if (rc) return rc;
+  for (ccmc_lattice *h : G.m) h->phases_done += 8 * nsweeps;
+  return CCMC_OK;
+}
+
+}  // namespace
+
 namespace ccmc {
 
 int batch_run(ccmc_batch *b, const std::vector<ccmc_lattice *> &lats, const int64_t *nsweeps,
               const double *beta, const double *Delta, const double *V, const double *J,
-              const int *obs_every) {
+              const int *obs_every, bool lockstep) {
   const int n = (int)lats.size();
   if (n > b->cap) return CCMC_E_INVAL;
   for (int i = 0; i < n; ++i) {
@@ -582,13 +704,52 @@ int batch_run(ccmc_batch *b, const std::vector<ccmc_lattice *> &lats, const int6
       if (h->stream != b->stream) CK(cudaStreamWaitEvent(h->stream, b->ev, 0));
     }
   }
-  // the rest on their own streams, overlapping the resident launch
+  // The large lattices: those at the same position with the same sweeps,
+  // observable interval and alignment advance in lock-step with one phase
+  // launch for all of them (on the batch stream); the others run the per-phase
+  // path on their own streams.  Both overlap the resident launch.
+  std::vector<char> used(n, 0);
+  int64_t off = 0;
   for (int i = 0; i < n; ++i) {
     ccmc_lattice *h = lats[i];
     const int64_t sites = 16 * h->g.cstride * 16;
-    if (nsweeps[i] == 0 || sites <= b->resident_max_sites) continue;
-    const int rc = ccmc_sweep(h, nsweeps[i], beta[i], Delta[i], V[i], J[i], obs_every[i]);
+    if (used[i] || nsweeps[i] == 0 || sites <= b->resident_max_sites) continue;
+    MultiGroup G{{h}, off, 0, (h->g.Cx & 15) == 0};
+    used[i] = 1;
+    for (int k = i + 1; k < n && lockstep; ++k) {
+      ccmc_lattice *o = lats[k];
+      if (used[k] || nsweeps[k] != nsweeps[i] || obs_every[k] != obs_every[i] ||
+          o->phases_done != h->phases_done || ((o->g.Cx & 15) == 0) != G.aligned ||
+          16 * o->g.cstride * 16 <= b->resident_max_sites)
+        continue;
+      G.m.push_back(o);
+      used[k] = 1;
+    }
+    // Small groups run better as separate streams, whose phases fill each
+    // other's tails; lock-step pays off for many lattices.
+    if ((int)G.m.size() < kLockstepMin) {
+      for (ccmc_lattice *o : G.m) {
+        const int k = (int)(std::find(lats.begin(), lats.end(), o) - lats.begin());
+        const int rc = ccmc_sweep(o, nsweeps[k], beta[k], Delta[k], V[k], J[k], obs_every[k]);
+        if (rc) return rc;
+      }
+      continue;
+    }
+    for (ccmc_lattice *o : G.m) {
+      const int k = (int)(std::find(lats.begin(), lats.end(), o) - lats.begin());
+      if (o->stream != b->stream) {
+        CK(cudaEventRecord(b->lat_ev[k], o->stream));
+        CK(cudaStreamWaitEvent(b->stream, b->lat_ev[k], 0));
+      }
+      const int rc = upload_params_on(o, beta[k], Delta[k], V[k], J[k], b->stream);
+      if (rc) return rc;
+    }
+    const int rc = run_multi(b, G, nsweeps[i], obs_every[i]);
     if (rc) return rc;
+    off += (int64_t)G.m.size();
+    CK(cudaEventRecord(b->ev, b->stream));
+    for (ccmc_lattice *o : G.m)
+      if (o->stream != b->stream) CK(cudaStreamWaitEvent(o->stream, b->ev, 0));
   }
   return CCMC_OK;
 }
@@ -638,6 +799,7 @@ int ccmc::batch_new(int cap, cudaStream_t stream, ccmc_batch **out) {
   const int64_t max_words = optin / 4 - kResTableWords - 64;
   if (b->resident_max_sites / 4 > max_words) b->resident_max_sites = max_words * 4;
   if (cudaMalloc(&b->d_jobs, sizeof(JobDesc) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_multi, sizeof(MultiJob) * count) != cudaSuccess ||
       cudaMalloc(&b->d_queue, sizeof(int)) != cudaSuccess)
     return fail(CCMC_E_NOMEM);
   if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
@@ -655,7 +817,10 @@ extern "C" {
 int ccmc_batch_destroy(ccmc_batch *b) {
   if (!b) return CCMC_E_INVAL;
   if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto &e : b->graphs)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
   cudaFree(b->d_jobs);
+  cudaFree(b->d_multi);
   cudaFree(b->d_queue);
   if (b->ev) cudaEventDestroy(b->ev);
   for (auto e : b->lat_ev)
@@ -686,7 +851,7 @@ int ccmc_batch_sweep(ccmc_batch *b, const int64_t *nsweeps, const double *beta,
                      const double *Delta, const double *V, const double *J, int obs_every) {
   if (!b || !nsweeps || !beta || !Delta || !V || !J) return CCMC_E_INVAL;
   std::vector<int> every(b->lats.size(), obs_every);
-  return ccmc::batch_run(b, b->lats, nsweeps, beta, Delta, V, J, every.data());
+  return ccmc::batch_run(b, b->lats, nsweeps, beta, Delta, V, J, every.data(), true);
 }
 
 int ccmc_batch_sync(ccmc_batch *b) {

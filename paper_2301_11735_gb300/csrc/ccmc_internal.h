@@ -45,7 +45,7 @@ struct Geo {
 
 // Per-lattice parameter tables in device memory (built on the host).
 struct DevTables {
-  uint16_t *thr16;      // kTableN: top half of each threshold (fast path)
+  uint32_t *thrhi;      // kThrHiWords: each threshold with its low half cleared (fast path)
   uint32_t *thr32;      // kTableN: full thresholds (exact path)
   uint32_t *trans_far;  // kTransN x 2 words: move entries, partner not a neighbour
   uint32_t *trans_near; // kTransN x 2 words: move entries, partner a nearest neighbour
@@ -54,16 +54,16 @@ struct DevTables {
 // Move entries are indexed by pair state pc = 4 code_a + code_b and the pair's
 // choice byte mod 12 (12 is a multiple of both q-set sizes, 4 and 6).
 constexpr int kTransN = 16 * 12;
-constexpr int kThr16Bytes = (kTableN + 1) / 2 * 4;
+constexpr int kThrHiWords = (kTableN + 1) / 2 * 2;  // padded to an even count
 
 struct LaunchCfg {
-  int phase_grid_cap = 152 * 8;
+  int phase_grid_cap = 152 * 3;  // one resident wave of phase_kernel (set at create)
 };
 
 // One lattice of a resident batch launch (device array, filled on the host).
 struct JobDesc {
   Geo g;                    // the lattice in global memory
-  const uint32_t *thr16;    // its tables
+  const uint32_t *thrhi;    // its tables
   const uint32_t *thr32;
   const uint32_t *trans_far;
   const uint32_t *trans_near;
@@ -75,8 +75,19 @@ struct JobDesc {
   int obs_every;
 };
 
+// One lattice of a lock-step multi-lattice phase launch: CTAs
+// [cta_begin, cta_begin + cta_count) of the grid work on it.
+struct MultiJob {
+  Geo g;
+  const uint32_t *thrhi;
+  const uint32_t *thr32;
+  const uint32_t *trans_far;
+  const uint32_t *trans_near;
+  int cta_begin, cta_count;
+};
+
 // Shared memory of the resident kernel besides the lattice words.
-constexpr int kResTableWords = ((kTableN + 1) / 2 + 1) / 2 * 2 + 4 * kTransN;
+constexpr int kResTableWords = kThrHiWords + 4 * kTransN;
 
 // Host-side table builders (ccmc_tables.cpp).
 void build_thresholds(double beta, double Delta, double V, double J, uint32_t *thr32);
@@ -88,6 +99,11 @@ cudaError_t launch_init(const Geo &g, int h, int64_t n_plus, int64_t n_minus, cu
 cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const LaunchCfg &cfg,
                          cudaStream_t s);
 int recount_grid(const Geo &g);
+// CTAs of phase_kernel that fit the device at once (one wave).
+int phase_resident_grid(bool aligned);
+// One colour phase of every lattice in d_jobs (all aligned or all not).
+cudaError_t launch_phase_multi(const MultiJob *d_jobs, int njobs, int grid, bool aligned,
+                               int64_t p_off, cudaStream_t s);
 cudaError_t launch_recount(const Geo &g, int64_t *partials, int64_t *ring, int64_t ring_cap,
                            int64_t *hist, int nbins, int64_t sweep_off, cudaStream_t s);
 cudaError_t launch_advance(int64_t *ctl, int64_t phases, cudaStream_t s);
@@ -107,8 +123,11 @@ int batch_new(int cap, cudaStream_t stream, ccmc_batch **out);
 
 // Sweep a list of lattices (at most the batch's capacity) with per-lattice
 // sweeps, parameters and observable intervals through the batch machinery.
+// lockstep: large lattices at the same position may share phase launches
+// (the launches are captured once per group and replayed, so the list should
+// be the same on every call).
 int batch_run(ccmc_batch *b, const std::vector<ccmc_lattice *> &lats, const int64_t *nsweeps,
               const double *beta, const double *Delta, const double *V, const double *J,
-              const int *obs_every);
+              const int *obs_every, bool lockstep);
 
 }  // namespace ccmc

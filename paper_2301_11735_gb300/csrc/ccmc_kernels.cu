@@ -68,17 +68,18 @@ __global__ void init_kernel(Geo g, int h, int64_t n_plus, int64_t n_minus) {
 // of a, the b window and the four neighbour windows of b; evaluates every
 // pair's move; stores the a word and XORs the changed b sites back.
 //
-// Per pair, with pc = 4 code_a + code_b and its 32-bit random word (16-bit
-// choice v, top half u of the acceptance word):
+// Per pair, with pc = 4 code_a + code_b and its 32-bit random word R (16-bit
+// choice v in the low half, top half u of the acceptance word in the high):
 //   entry  = trans[pc][v mod 12]  -> base, byte coefficients, pc XOR npc
 //   index  = dp4a(coefficients, (D8, GA, GB, 0), base)  (threshold index)
-//   accept = u < thr16[index]; a tie, or v >= 65532, is settled exactly by the
-//            slow path with the pair's SLOW random words (about 1 pair in 10^4).
-constexpr int kThr16Words = (kTableN + 1) / 2;
-
+//   accept = R < thrhi[index], i.e. u < the threshold's top half (v < 2^16)
+// The fast decision is always applied.  A tie of the top halves, or a choice
+// field v >= 65532, marks the pair rare: the exact path then undoes the fast
+// decision and applies the exact one with the pair's SLOW random words
+// (about one pair in 10^4).
 struct PhaseSmem {
   uint2 trans[kTransN];
-  uint32_t thr16[kThr16Words];
+  uint32_t thrhi[kThrHiWords];
   Sched sched;
 };
 
@@ -140,7 +141,7 @@ __device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, in
 
 template <bool kAligned>
 __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
-                                           const uint32_t *thr16, const uint32_t *thr32, int j,
+                                           const uint32_t *thrhi, const uint32_t *thr32, int j,
                                            int w, uint64_t P) {
   const int s0 = w << 4;
   const int n = kAligned ? 16 : min(16, g.Cx - s0);
@@ -195,26 +196,26 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
                          : b == 2 ? prmt(x23[k], gbk[k], 0x8610u)
                                   : prmt(x23[k], gbk[k], 0x8732u);
       const uint32_t pc = (((t & 1) ? pcO : pcE) >> (4 * (t >> 1))) & 15u;
-      const uint32_t v = R & 0xFFFFu, uh = R >> 16;
+      const uint32_t v = R & 0xFFFFu;
       const uint32_t r12 = v - 12u * ((v * 43691u) >> 19);  // v mod 12 for v < 2^16
       const uint2 e = trans[pc * 12u + r12];
       const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
-      const uint32_t th = (thr16[idx >> 1] >> (16 * (idx & 1))) & 0xFFFFu;
-      if (v >= 65532u || uh == th) {
-        slow |= 1u << t;
-      } else if (uh < th) {
-        const uint32_t x = e.y >> 24;
-        if (t & 1)
-          dO |= x << (4 * (t >> 1));
-        else
-          dE |= x << (4 * (t >> 1));
-      }
+      const uint32_t TH = thrhi[idx];
+      const bool rare = ((R ^ TH) < 0x10000u) | (v >= 65532u);
+      slow |= (uint32_t)rare << t;
+      // move bits of this pair (e.y bits 24-27) placed at its 4-bit lane
+      const int lsh = 4 * (t >> 1);
+      const uint32_t xm = (lsh <= 24 ? (e.y >> (24 - lsh)) : (e.y << (lsh - 24))) & (15u << lsh);
+      if (t & 1)
+        dO |= R < TH ? xm : 0u;
+      else
+        dE |= R < TH ? xm : 0u;
     }
   }
   uint32_t dA = ((dE >> 2) & 0x33333333u) | (((dO >> 2) & 0x33333333u) << 2);
   uint32_t dB = (dE & 0x33333333u) | ((dO & 0x33333333u) << 2);
 
-  // ---- exact path for the undecided pairs
+  // ---- exact path for the rare pairs: undo the fast decision, apply the exact one
   while (slow) {
     const int t = __ffs(slow) - 1;
     slow &= slow - 1u;
@@ -224,6 +225,21 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
     const int qw = t & 3;
     const uint32_t R = qw == 0 ? mv.x : qw == 1 ? mv.y : qw == 2 ? mv.z : mv.w;
     const uint32_t v = R & 0xFFFFu, uh = R >> 16;
+    const int sh = 4 * (t >> 1);
+    const uint32_t sa4 = (((t & 1) ? sa.so : sa.se) >> sh) & 15u;
+    const uint32_t sb4 = (((t & 1) ? sb.so : sb.se) >> sh) & 15u;
+    const uint32_t ga4 = (((t & 1) ? sa.go : sa.ge) >> sh) & 15u;
+    const uint32_t gb4 = (((t & 1) ? sb.go : sb.ge) >> sh) & 15u;
+    const uint32_t env = (sa4 + 8u - sb4) | (ga4 << 8) | (gb4 << 16);
+    {  // the fast path's decision for this pair, to undo it
+      const uint2 ef = trans[pc * 12u + v % 12u];
+      const int idxf = __dp4a((int)ef.y, (int)env, (int)ef.x);
+      if (R < thrhi[idxf]) {
+        const uint32_t x = ef.y >> 24;
+        dA ^= (x >> 2) << (2 * t);
+        dB ^= (x & 3u) << (2 * t);
+      }
+    }
     const uint64_t kk = (uint64_t)j * g.Cx + s0 + t;
     const U4 sl = philox((uint32_t)kk, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, g.k0, g.k1);
     uint32_t r;
@@ -234,19 +250,13 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
     else
       continue;  // keep the current configuration
     const uint2 e = trans[pc * 12u + r];
-    const int sh = 4 * (t >> 1);
-    const uint32_t sa4 = (((t & 1) ? sa.so : sa.se) >> sh) & 15u;
-    const uint32_t sb4 = (((t & 1) ? sb.so : sb.se) >> sh) & 15u;
-    const uint32_t ga4 = (((t & 1) ? sa.go : sa.ge) >> sh) & 15u;
-    const uint32_t gb4 = (((t & 1) ? sb.go : sb.ge) >> sh) & 15u;
-    const uint32_t env = (sa4 + 8u - sb4) | (ga4 << 8) | (gb4 << 16);
     const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
     const uint32_t thr = thr32[idx];
     const uint32_t uu = (uh << 16) | (sl.x & 0xFFFFu);
     if (thr == 0xFFFFFFFFu || uu < thr) {
       const uint32_t x = e.y >> 24;
-      dA |= (x >> 2) << (2 * t);
-      dB |= (x & 3u) << (2 * t);
+      dA ^= (x >> 2) << (2 * t);
+      dB ^= (x & 3u) << (2 * t);
     }
   }
   if constexpr (!kAligned) {
@@ -276,17 +286,25 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
 }
 
 template <bool kAligned>
-__global__ void __launch_bounds__(256) phase_kernel(Geo g, const uint32_t *thr16,
+__global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *thrhi,
                                                     const uint32_t *thr32,
                                                     const uint32_t *trans_far,
                                                     const uint32_t *trans_near, int64_t p_off) {
   __shared__ PhaseSmem sm;
+  // The tables come from host uploads that precede the whole launch chain, so
+  // they are loaded before waiting for the previous kernel of the stream (which
+  // lets this prologue overlap its tail under programmatic dependent launch).
+  for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) sm.thrhi[t] = thrhi[t];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // The next kernel may launch now: with one resident wave its blocks only take
+  // the slots of blocks that finish, and it waits for this whole grid before
+  // touching the lattice.
+  asm volatile("griddepcontrol.launch_dependents;");
   const uint64_t P = (uint64_t)(g.ctl[kCtlPhaseBase] + p_off);
   if (threadIdx.x < 32) {
     const Sched s = draw_schedule(g, P);
     if (threadIdx.x == 0) sm.sched = s;
   }
-  for (int t = threadIdx.x; t < kThr16Words; t += blockDim.x) sm.thr16[t] = thr16[t];
   __syncthreads();
   const Sched sc = sm.sched;
   const uint32_t *trans = sc.near ? trans_near : trans_far;
@@ -300,7 +318,54 @@ __global__ void __launch_bounds__(256) phase_kernel(Geo g, const uint32_t *thr16
   int j = wid / g.W, w = wid - j * g.W;
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
-    phase_word<kAligned>(g, u, sm.trans, sm.thr16, thr32, j, w, P);
+    phase_word<kAligned>(g, u, sm.trans, sm.thrhi, thr32, j, w, P);
+    w += sw;
+    j += sj;
+    if (w >= g.W) {
+      w -= g.W;
+      ++j;
+    }
+  }
+}
+
+// Lock-step phase of several lattices in one launch: each CTA works on one
+// lattice (its share of the grid is proportional to the lattice's words), with
+// that lattice's tables, phase counter and schedule.
+template <bool kAligned>
+__global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__restrict__ jobs,
+                                                             int njobs, int64_t p_off) {
+  __shared__ PhaseSmem sm;
+  __shared__ int s_job;
+  if (threadIdx.x == 0) {
+    int j = 0;
+    while (j + 1 < njobs && (int)blockIdx.x >= jobs[j + 1].cta_begin) ++j;
+    s_job = j;
+  }
+  __syncthreads();
+  const MultiJob &J = jobs[s_job];
+  const Geo g = J.g;
+  for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) sm.thrhi[t] = J.thrhi[t];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+  const uint64_t P = (uint64_t)(g.ctl[kCtlPhaseBase] + p_off);
+  if (threadIdx.x < 32) {
+    const Sched sc = draw_schedule(g, P);
+    if (threadIdx.x == 0) sm.sched = sc;
+  }
+  __syncthreads();
+  const Sched sc = sm.sched;
+  const uint32_t *trans = sc.near ? J.trans_near : J.trans_far;
+  for (int t = threadIdx.x; t < kTransN; t += blockDim.x)
+    sm.trans[t] = make_uint2(trans[2 * t], trans[2 * t + 1]);
+  __syncthreads();
+  const PhaseU u = phase_uniform(g, sc);
+  const int nw = g.Cy * g.W;
+  int wid = ((int)blockIdx.x - J.cta_begin) * blockDim.x + threadIdx.x;
+  const int stride = J.cta_count * blockDim.x;
+  int j = wid / g.W, w = wid - j * g.W;
+  const int sj = stride / g.W, sw = stride - sj * g.W;
+  for (; wid < nw; wid += stride) {
+    phase_word<kAligned>(g, u, sm.trans, sm.thrhi, J.thr32, j, w, P);
     w += sw;
     j += sj;
     if (w >= g.W) {
@@ -372,6 +437,8 @@ __device__ __forceinline__ void count_words(const Geo &g, int64_t tid, int64_t n
 }
 
 __global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   int c[7] = {0, 0, 0, 0, 0, 0, 0};  // Nc, BV, BJ, M, Ms, S, Ss
   count_words(g, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
               c);
@@ -439,8 +506,8 @@ __global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
 __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict__ jobs, int njobs,
                                                        int *queue) {
   extern __shared__ __align__(16) uint32_t dyn[];
-  uint32_t *s_thr16 = dyn;
-  uint2 *s_far = reinterpret_cast<uint2 *>(dyn + ((kTableN + 1) / 2 + 1) / 2 * 2);
+  uint32_t *s_thrhi = dyn;
+  uint2 *s_far = reinterpret_cast<uint2 *>(dyn + kThrHiWords);
   uint2 *s_near = s_far + kTransN;
   uint32_t *s_words = dyn + kResTableWords;
   __shared__ Sched s_sched;
@@ -455,7 +522,7 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
     const JobDesc &J = jobs[job];
     const Geo g = J.g;
     const int64_t nw = 16 * g.cstride;
-    for (int t = threadIdx.x; t < (kTableN + 1) / 2; t += blockDim.x) s_thr16[t] = J.thr16[t];
+    for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) s_thrhi[t] = J.thrhi[t];
     for (int t = threadIdx.x; t < kTransN; t += blockDim.x) {
       s_far[t] = make_uint2(J.trans_far[2 * t], J.trans_far[2 * t + 1]);
       s_near[t] = make_uint2(J.trans_near[2 * t], J.trans_near[2 * t + 1]);
@@ -483,9 +550,9 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
         for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
           const int j = wid / g.W, w = wid - j * g.W;
           if (aligned)
-            phase_word<true>(gs, u, tr, s_thr16, J.thr32, j, w, P);
+            phase_word<true>(gs, u, tr, s_thrhi, J.thr32, j, w, P);
           else
-            phase_word<false>(gs, u, tr, s_thr16, J.thr32, j, w, P);
+            phase_word<false>(gs, u, tr, s_thrhi, J.thr32, j, w, P);
         }
         __syncthreads();
       }
@@ -542,7 +609,10 @@ cudaError_t launch_resident(const JobDesc *d_jobs, int njobs, int *d_queue, int 
 }
 
 // ============================================================================
-__global__ void advance_kernel(int64_t *ctl, int64_t phases) { ctl[kCtlPhaseBase] += phases; }
+__global__ void advance_kernel(int64_t *ctl, int64_t phases) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  ctl[kCtlPhaseBase] += phases;
+}
 
 __global__ void set_ctl_kernel(int64_t *ctl, int64_t phase_base) {
   for (int k = threadIdx.x; k < kCtlWords; k += blockDim.x) ctl[k] = 0;
@@ -600,6 +670,25 @@ __global__ void philox_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
 
 // ============================================================================
 // Launchers.
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous kernel of the stream drains, and waits for it (griddepcontrol)
+// before touching anything that kernel writes.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 static int grid_for(int64_t items, int block, int cap) {
   int64_t b = (items + block - 1) / block;
   if (b > cap) b = cap;
@@ -611,16 +700,31 @@ cudaError_t launch_init(const Geo &g, int h, int64_t n_plus, int64_t n_minus, cu
   return cudaGetLastError();
 }
 
+int phase_resident_grid(bool aligned) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const cudaError_t e =
+      aligned ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_kernel<true>, 256, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_kernel<false>, 256, 0);
+  if (e != cudaSuccess || per_sm < 1 || sms < 1) return 152 * 3;
+  return per_sm * sms;
+}
+
 cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const LaunchCfg &cfg,
                          cudaStream_t s) {
   const int64_t nw = (int64_t)g.Cy * g.W;
   const int grid = grid_for(nw, 256, cfg.phase_grid_cap);
-  const uint32_t *thr16 = reinterpret_cast<const uint32_t *>(t.thr16);
+  const uint32_t *thrhi = t.thrhi, *thr32 = t.thr32, *tf = t.trans_far, *tn = t.trans_near;
   if ((g.Cx & 15) == 0)
-    phase_kernel<true><<<grid, 256, 0, s>>>(g, thr16, t.thr32, t.trans_far, t.trans_near, p_off);
-  else
-    phase_kernel<false><<<grid, 256, 0, s>>>(g, thr16, t.thr32, t.trans_far, t.trans_near, p_off);
-  return cudaGetLastError();
+    return launch_pdl(phase_kernel<true>, grid, 256, s, g, thrhi, thr32, tf, tn, p_off);
+  return launch_pdl(phase_kernel<false>, grid, 256, s, g, thrhi, thr32, tf, tn, p_off);
+}
+
+cudaError_t launch_phase_multi(const MultiJob *d_jobs, int njobs, int grid, bool aligned,
+                               int64_t p_off, cudaStream_t s) {
+  if (aligned) return launch_pdl(phase_multi_kernel<true>, grid, 256, s, d_jobs, njobs, p_off);
+  return launch_pdl(phase_multi_kernel<false>, grid, 256, s, d_jobs, njobs, p_off);
 }
 
 int recount_grid(const Geo &g) { return grid_for(16 * g.cstride, 256, 152 * 4); }
@@ -628,13 +732,11 @@ int recount_grid(const Geo &g) { return grid_for(16 * g.cstride, 256, 152 * 4); 
 cudaError_t launch_recount(const Geo &g, int64_t *partials, int64_t *ring, int64_t ring_cap,
                            int64_t *hist, int nbins, int64_t sweep_off, cudaStream_t s) {
   RecountArgs a{partials, ring, ring_cap, hist, nbins, sweep_off};
-  recount_kernel<<<recount_grid(g), 256, 0, s>>>(g, a);
-  return cudaGetLastError();
+  return launch_pdl(recount_kernel, recount_grid(g), 256, s, g, a);
 }
 
 cudaError_t launch_advance(int64_t *ctl, int64_t phases, cudaStream_t s) {
-  advance_kernel<<<1, 1, 0, s>>>(ctl, phases);
-  return cudaGetLastError();
+  return launch_pdl(advance_kernel, 1, 1, s, ctl, phases);
 }
 
 cudaError_t launch_set_ctl(int64_t *ctl, int64_t phase_base, cudaStream_t s) {

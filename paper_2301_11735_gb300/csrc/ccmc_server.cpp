@@ -206,7 +206,7 @@ void ccmc_server::run() {
       every[i] = r.req.obs_every;
     }
     int rc = ccmc::batch_run(batch, lats, sw.data(), beta.data(), Delta.data(), V.data(), J.data(),
-                             every.data());
+                             every.data(), false);
     if (rc == CCMC_OK && cudaStreamSynchronize(stream) != cudaSuccess) rc = CCMC_E_CUDA;
     for (int i = 0; i < n && rc == CCMC_OK; ++i) rc = ccmc_sync(lats[i]);
     {

@@ -152,3 +152,31 @@ def test_autotuner_picks_a_valid_shape_and_results_stay_exact(cc, tmp_path, monk
     ref = _run_single(cc, shapes, nsw, obs_every=2)
     for (s1, r1), (s2, r2) in zip(got, ref):
         assert np.array_equal(s1, s2) and np.array_equal(r1, r2)
+
+
+@pytest.mark.parametrize("shapes", [[(512, 512)] * 8 + [(256, 256)],
+                                    [(516, 260)] * 8 + [(1024, 1024)]])
+def test_large_lattices_in_lockstep_equal_individual_runs(cc, shapes):
+    """Eight or more large lattices at the same sweep advance with one phase
+    launch for all of them (a lock-step group); each must still match its own
+    run.  A small resident limit sends every lattice down the large path."""
+    n = len(shapes)
+    seeds = [20 + i for i in range(n)]
+    Ts = [0.2 + 0.25 * i for i in range(n)]
+    lats = []
+    for (Lx, Ly), sd in zip(shapes, seeds):
+        lat = cc.Lattice(Lx, Ly)
+        lat.init_constrained(sd, 0.1, 0.3)
+        lats.append(lat)
+    with cc.Batch(lats) as b:
+        b.config(256, 1024, 2)
+        for _ in range(2):  # the second call replays the captured group graph
+            b.sweep(17, [1 / T for T in Ts], 0.0, 0.5, 1.0, obs_every=1)
+        b.sync()
+    for (Lx, Ly), sd, T, lat in zip(shapes, seeds, Ts, lats):
+        with cc.Lattice(Lx, Ly) as one:
+            one.init_constrained(sd, 0.1, 0.3)
+            one.sweep(34, 1 / T, 0.0, 0.5, 1.0, obs_every=1)
+            assert np.array_equal(one.get_state(), lat.get_state()), (Lx, Ly, T)
+            assert np.array_equal(one.obs_series(), lat.obs_series()), (Lx, Ly, T)
+        lat.close()
