@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <new>
@@ -253,6 +254,7 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   const uint64_t N = (uint64_t)Lx * (uint64_t)Ly;
   g.rej = (0 - N) % N;
   h->cfg.phase_grid_cap = phase_resident_grid((g.Cx & 15) == 0);
+  if (tile_path_ok(g) && !std::getenv("CCMC_NO_TILE")) h->cfg.tile_grid = tile_resident_grid();
   while (((int64_t)1 << (2 * h->h)) < (int64_t)N) ++h->h;
   h->ring_cap = obs_capacity > 0 ? obs_capacity : 4096;
   cudaGetDevice(&h->device);

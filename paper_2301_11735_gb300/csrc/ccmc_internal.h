@@ -58,6 +58,7 @@ constexpr int kThrHiWords = (kTableN + 1) / 2 * 2;  // padded to an even count
 
 struct LaunchCfg {
   int phase_grid_cap = 152 * 3;  // one resident wave of phase_kernel (set at create)
+  int tile_grid = 0;             // > 0: tile-staged phases, this many CTAs at most
 };
 
 // One lattice of a resident batch launch (device array, filled on the host).
@@ -101,6 +102,9 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
 int recount_grid(const Geo &g);
 // CTAs of phase_kernel that fit the device at once (one wave).
 int phase_resident_grid(bool aligned);
+// Whether a lattice can take the tile-staged phase kernel, and its one wave.
+bool tile_path_ok(const Geo &g);
+int tile_resident_grid();
 // One colour phase of every lattice in d_jobs (all aligned or all not).
 cudaError_t launch_phase_multi(const MultiJob *d_jobs, int njobs, int grid, bool aligned,
                                int64_t p_off, cudaStream_t s);

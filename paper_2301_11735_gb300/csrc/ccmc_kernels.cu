@@ -139,23 +139,26 @@ __device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, in
   }
 }
 
+// j: the pair's row in the class (keys the random streams); jr: the row of the
+// a word in u's arrays (j itself for the lattice in global memory, the row
+// inside a staged tile otherwise).
 template <bool kAligned>
 __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
                                            const uint32_t *thrhi, const uint32_t *thr32, int j,
-                                           int w, uint64_t P) {
+                                           int jr, int w, uint64_t P) {
   const int s0 = w << 4;
   const int n = kAligned ? 16 : min(16, g.Cx - s0);
   const int Cy = g.Cy;
 
   // ---- gather: the a word, the b window and the eight neighbour windows
-  uint32_t *rowA = const_cast<uint32_t *>(u.cA) + j * g.W;
+  uint32_t *rowA = const_cast<uint32_t *>(u.cA) + jr * g.W;
   const uint32_t A = rowA[w];
   Sums sa{0u, 0u, 0u, 0u}, sb{0u, 0u, 0u, 0u};
-  add_neighbour(sa, window<kAligned>(u.cAL, g, j, w, u.offAL, n));
-  add_neighbour(sa, window<kAligned>(u.cAR, g, j, w, u.offAR, n));
-  add_neighbour(sa, u.cAU[wrap(j + u.dyAU, Cy) * g.W + w]);
-  add_neighbour(sa, u.cAD[wrap(j + u.dyAD, Cy) * g.W + w]);
-  const int jb = wrap(j + u.qy, Cy);
+  add_neighbour(sa, window<kAligned>(u.cAL, g, jr, w, u.offAL, n));
+  add_neighbour(sa, window<kAligned>(u.cAR, g, jr, w, u.offAR, n));
+  add_neighbour(sa, u.cAU[wrap(jr + u.dyAU, Cy) * g.W + w]);
+  add_neighbour(sa, u.cAD[wrap(jr + u.dyAD, Cy) * g.W + w]);
+  const int jb = wrap(jr + u.qy, Cy);
   const uint32_t B = window<kAligned>(u.cB, g, jb, w, u.offB, n);
   add_neighbour(sb, window<kAligned>(u.cBL, g, jb, w, u.offBL, n));
   add_neighbour(sb, window<kAligned>(u.cBR, g, jb, w, u.offBR, n));
@@ -186,6 +189,7 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
     if (!kAligned && 4 * b >= n) break;
     const U4 r = philox(gbase + (uint32_t)b, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0,
                         g.k1);
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;  // smallest R ^ TH and largest v of the group
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int t = 4 * b + k;
@@ -201,29 +205,38 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
       const uint2 e = trans[pc * 12u + r12];
       const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
       const uint32_t TH = thrhi[idx];
-      const bool rare = ((R ^ TH) < 0x10000u) | (v >= 65532u);
-      slow |= (uint32_t)rare << t;
-      // move bits of this pair (e.y bits 24-27) placed at its 4-bit lane
-      const int lsh = 4 * (t >> 1);
-      const uint32_t xm = (lsh <= 24 ? (e.y >> (24 - lsh)) : (e.y << (lsh - 24))) & (15u << lsh);
+      mn = min(mn, R ^ TH);
+      mx = max(mx, v);
+      // move bits of this pair (e.y bits 24-27) added at its 4-bit lane
+      const uint32_t xm = (e.y >> 24) * (1u << (4 * (t >> 1)));
       if (t & 1)
-        dO |= R < TH ? xm : 0u;
+        dO += R < TH ? xm : 0u;
       else
-        dE |= R < TH ? xm : 0u;
+        dE += R < TH ? xm : 0u;
     }
+    // a tie of the top halves (R ^ TH < 2^16) or a choice field >= 65532 makes
+    // the group's pairs go through the exact path
+    if (mn < 0x10000u || mx >= 65532u) slow |= 0xFu << (4 * b);
   }
   uint32_t dA = ((dE >> 2) & 0x33333333u) | (((dO >> 2) & 0x33333333u) << 2);
   uint32_t dB = (dE & 0x33333333u) | ((dO & 0x33333333u) << 2);
 
-  // ---- exact path for the rare pairs: undo the fast decision, apply the exact one
+  // ---- exact path for the flagged groups: for each truly rare pair, undo the
+  // fast decision and apply the exact one
+  U4 mv{0u, 0u, 0u, 0u};
+  int mv_group = -1;
   while (slow) {
     const int t = __ffs(slow) - 1;
     slow &= slow - 1u;
-    const uint32_t pc = (((A >> (2 * t)) & 3u) << 2) | ((B >> (2 * t)) & 3u);
-    const U4 mv = philox(gbase + (uint32_t)(t >> 2), (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE,
-                         g.k0, g.k1);
+    if (!kAligned && t >= n) continue;
+    if ((t >> 2) != mv_group) {
+      mv_group = t >> 2;
+      mv = philox(gbase + (uint32_t)mv_group, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0,
+                  g.k1);
+    }
     const int qw = t & 3;
     const uint32_t R = qw == 0 ? mv.x : qw == 1 ? mv.y : qw == 2 ? mv.z : mv.w;
+    const uint32_t pc = (((A >> (2 * t)) & 3u) << 2) | ((B >> (2 * t)) & 3u);
     const uint32_t v = R & 0xFFFFu, uh = R >> 16;
     const int sh = 4 * (t >> 1);
     const uint32_t sa4 = (((t & 1) ? sa.so : sa.se) >> sh) & 15u;
@@ -231,14 +244,14 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
     const uint32_t ga4 = (((t & 1) ? sa.go : sa.ge) >> sh) & 15u;
     const uint32_t gb4 = (((t & 1) ? sb.go : sb.ge) >> sh) & 15u;
     const uint32_t env = (sa4 + 8u - sb4) | (ga4 << 8) | (gb4 << 16);
-    {  // the fast path's decision for this pair, to undo it
-      const uint2 ef = trans[pc * 12u + v % 12u];
-      const int idxf = __dp4a((int)ef.y, (int)env, (int)ef.x);
-      if (R < thrhi[idxf]) {
-        const uint32_t x = ef.y >> 24;
-        dA ^= (x >> 2) << (2 * t);
-        dB ^= (x & 3u) << (2 * t);
-      }
+    // the fast path's decision for this pair
+    const uint2 ef = trans[pc * 12u + v % 12u];
+    const uint32_t THf = thrhi[__dp4a((int)ef.y, (int)env, (int)ef.x)];
+    if ((R ^ THf) >= 0x10000u && v < 65532u) continue;  // not rare: the fast decision stands
+    if (R < THf) {  // undo it
+      const uint32_t x = ef.y >> 24;
+      dA ^= (x >> 2) << (2 * t);
+      dB ^= (x & 3u) << (2 * t);
     }
     const uint64_t kk = (uint64_t)j * g.Cx + s0 + t;
     const U4 sl = philox((uint32_t)kk, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, g.k0, g.k1);
@@ -318,12 +331,192 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *th
   int j = wid / g.W, w = wid - j * g.W;
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
-    phase_word<kAligned>(g, u, sm.trans, sm.thrhi, thr32, j, w, P);
+    phase_word<kAligned>(g, u, sm.trans, sm.thrhi, thr32, j, j, w, P);
     w += sw;
     j += sj;
     if (w >= g.W) {
       w -= g.W;
       ++j;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Tile-staged phase (lattices whose class rows are W words with W dividing 256
+// and a multiple of 4, and Cy a multiple of R = 256 / W).  A tile is R
+// consecutive rows of the a-class (256 words, one per thread).  One thread
+// stages the tile's ten row bands -- the a rows, the b rows and the rows of
+// all eight neighbour classes, each band R full rows -- into shared memory with
+// bulk asynchronous copies that complete on an mbarrier; two buffers let the
+// next tile's copies run while this tile is evaluated.  The per-word code then
+// reads every window from shared memory, and the a and b bands go back with
+// bulk copies.  No two tiles of a phase write the same rows (each b row is the
+// partner row of exactly one a row), so global memory sees no atomics.
+constexpr int kTileWords = 256;
+constexpr int kBands = 10;
+constexpr int kWaitSpins = 1 << 20;  // bounded mbarrier waits
+
+struct TileSmem {
+  uint32_t thrhi[kThrHiWords];
+  uint2 trans[kTransN];
+  alignas(128) uint32_t band[2][kBands][kTileWords];
+  alignas(8) unsigned long long mbar[2];
+  Sched sched;
+  int err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kWaitSpins; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      :
+      : "r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void *dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+               :
+               : "l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+
+// Row band: R rows of one class starting at row r0 (periodic in Cy).
+struct Band {
+  const uint32_t *cls;
+  int dy;  // first row relative to the tile's first a row
+};
+
+__global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_t *thrhi,
+                                                            const uint32_t *thr32,
+                                                            const uint32_t *trans_far,
+                                                            const uint32_t *trans_near,
+                                                            int64_t p_off) {
+  __shared__ TileSmem sm;
+  for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) sm.thrhi[t] = thrhi[t];
+  if (threadIdx.x == 0) {
+    sm.err = 0;
+    for (int b = 0; b < 2; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar[b])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+  const uint64_t P = (uint64_t)(g.ctl[kCtlPhaseBase] + p_off);
+  if (threadIdx.x < 32) {
+    const Sched sc = draw_schedule(g, P);
+    if (threadIdx.x == 0) sm.sched = sc;
+  }
+  __syncthreads();
+  const Sched sc = sm.sched;
+  const uint32_t *trans = sc.near ? trans_near : trans_far;
+  for (int t = threadIdx.x; t < kTransN; t += blockDim.x)
+    sm.trans[t] = make_uint2(trans[2 * t], trans[2 * t + 1]);
+  const PhaseU u = phase_uniform(g, sc);
+  const int W = g.W, R = kTileWords / W, Cy = g.Cy;
+  const Band bands[kBands] = {{u.cA, 0},          {u.cAL, 0},          {u.cAR, 0},
+                              {u.cAU, u.dyAU},    {u.cAD, u.dyAD},     {u.cB, u.qy},
+                              {u.cBL, u.qy},      {u.cBR, u.qy},       {u.cBU, u.qy + u.dyBU},
+                              {u.cBD, u.qy + u.dyBD}};
+  const int ntiles = Cy / R;
+  const uint32_t row_bytes = (uint32_t)W * 4u;
+
+  // thread 0 stages tile `tile` into buffer `buf`
+  auto stage = [&](int tile, int buf) {
+    const uint32_t bar = smem_u32(&sm.mbar[buf]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((uint32_t)(kBands * kTileWords * 4))
+                 : "memory");
+    const int j0 = tile * R;
+    for (int k = 0; k < kBands; ++k) {
+      int r0 = (j0 + bands[k].dy) % Cy;
+      if (r0 < 0) r0 += Cy;
+      const int n1 = min(R, Cy - r0);
+      const uint32_t dst = smem_u32(&sm.band[buf][k][0]);
+      bulk_load(dst, bands[k].cls + (int64_t)r0 * W, (uint32_t)n1 * row_bytes, bar);
+      if (n1 < R) bulk_load(dst + (uint32_t)n1 * row_bytes, bands[k].cls, (uint32_t)(R - n1) * row_bytes, bar);
+    }
+  };
+
+  uint32_t par0 = 0u, par1 = 0u;  // phase parity of each buffer's mbarrier
+  int buf = 0;
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) stage(tile, 0);
+  __syncthreads();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    if (threadIdx.x == 0 && next < ntiles) {
+      // the other buffer's previous bulk stores must have finished reading it
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      stage(next, buf ^ 1);
+    }
+    if (!mbar_wait(smem_u32(&sm.mbar[buf]), buf ? par1 : par0)) sm.err = 1;
+    if (buf)
+      par1 ^= 1u;
+    else
+      par0 ^= 1u;
+    __syncthreads();
+    if (sm.err) break;
+    // evaluate this thread's word from the staged bands
+    PhaseU lu = u;
+    lu.cA = sm.band[buf][0];
+    lu.cAL = sm.band[buf][1];
+    lu.cAR = sm.band[buf][2];
+    lu.cAU = sm.band[buf][3];
+    lu.cAD = sm.band[buf][4];
+    lu.cB = sm.band[buf][5];
+    lu.cBL = sm.band[buf][6];
+    lu.cBR = sm.band[buf][7];
+    lu.cBU = sm.band[buf][8];
+    lu.cBD = sm.band[buf][9];
+    lu.dyAU = lu.dyAD = lu.qy = lu.dyBU = lu.dyBD = 0;
+    const int jr = threadIdx.x / W, w = threadIdx.x - jr * W;
+    phase_word<true>(g, lu, sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // write the a and b bands back
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const int j0 = tile * R;
+      bulk_store(const_cast<uint32_t *>(u.cA) + (int64_t)j0 * W, smem_u32(&sm.band[buf][0][0]),
+                 (uint32_t)R * row_bytes);
+      int rb = (j0 + u.qy) % Cy;
+      if (rb < 0) rb += Cy;
+      const int n1 = min(R, Cy - rb);
+      const uint32_t src = smem_u32(&sm.band[buf][5][0]);
+      bulk_store(const_cast<uint32_t *>(u.cB) + (int64_t)rb * W, src, (uint32_t)n1 * row_bytes);
+      if (n1 < R)
+        bulk_store(const_cast<uint32_t *>(u.cB), src + (uint32_t)n1 * row_bytes,
+                   (uint32_t)(R - n1) * row_bytes);
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    buf ^= 1;
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (sm.err) {
+      // give copies still in flight a bounded chance to land before exiting
+      mbar_wait(smem_u32(&sm.mbar[0]), par0);
+      mbar_wait(smem_u32(&sm.mbar[1]), par1);
+      g.ctl[kCtlStatus] = 1;
     }
   }
 }
@@ -365,7 +558,7 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
   int j = wid / g.W, w = wid - j * g.W;
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
-    phase_word<kAligned>(g, u, sm.trans, sm.thrhi, J.thr32, j, w, P);
+    phase_word<kAligned>(g, u, sm.trans, sm.thrhi, J.thr32, j, j, w, P);
     w += sw;
     j += sj;
     if (w >= g.W) {
@@ -550,9 +743,9 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
         for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
           const int j = wid / g.W, w = wid - j * g.W;
           if (aligned)
-            phase_word<true>(gs, u, tr, s_thrhi, J.thr32, j, w, P);
+            phase_word<true>(gs, u, tr, s_thrhi, J.thr32, j, j, w, P);
           else
-            phase_word<false>(gs, u, tr, s_thrhi, J.thr32, j, w, P);
+            phase_word<false>(gs, u, tr, s_thrhi, J.thr32, j, j, w, P);
         }
         __syncthreads();
       }
@@ -711,9 +904,31 @@ int phase_resident_grid(bool aligned) {
   return per_sm * sms;
 }
 
+bool tile_path_ok(const Geo &g) {
+  return (g.Cx & 15) == 0 && (g.W & 3) == 0 && g.W <= kTileWords && kTileWords % g.W == 0 &&
+         g.Cy % (kTileWords / g.W) == 0;
+}
+
+int tile_resident_grid() {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel, 256, 0) !=
+          cudaSuccess ||
+      per_sm < 1 || sms < 1)
+    return 152 * 2;
+  return per_sm * sms;
+}
+
 cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const LaunchCfg &cfg,
                          cudaStream_t s) {
   const int64_t nw = (int64_t)g.Cy * g.W;
+  if (cfg.tile_grid > 0) {
+    const int64_t tiles = nw / kTileWords;
+    const int grid = (int)(tiles < cfg.tile_grid ? tiles : cfg.tile_grid);
+    return launch_pdl(phase_tile_kernel, grid, 256, s, g, t.thrhi, t.thr32, t.trans_far,
+                      t.trans_near, p_off);
+  }
   const int grid = grid_for(nw, 256, cfg.phase_grid_cap);
   const uint32_t *thrhi = t.thrhi, *thr32 = t.thr32, *tf = t.trans_far, *tn = t.trans_near;
   if ((g.Cx & 15) == 0)

@@ -247,3 +247,64 @@ def test_phase_steps_mixed_with_sweeps(cc):
         got = lat.obs_series()
         assert np.array_equal(got[-2:], rec)
         assert got[0, 0] == 3  # the record of the sweep the phases left open
+
+
+TILE_SHAPES = [(256, 256), (512, 128), (1024, 64), (2048, 32)]
+
+
+def _lattice(cc, Lx, Ly, tile: bool):
+    """A lattice on the tile-staged phase path (bulk copies into shared memory)
+    or, with CCMC_NO_TILE set at creation, on the direct-window path."""
+    import os
+
+    if tile:
+        os.environ.pop("CCMC_NO_TILE", None)
+        return cc.Lattice(Lx, Ly)
+    os.environ["CCMC_NO_TILE"] = "1"
+    try:
+        return cc.Lattice(Lx, Ly)
+    finally:
+        os.environ.pop("CCMC_NO_TILE", None)
+
+
+@pytest.mark.parametrize("shape", TILE_SHAPES)
+@pytest.mark.parametrize("tile", [True, False])
+def test_tile_and_direct_paths_match_oracle(cc, shape, tile):
+    Lx, Ly = shape
+    seed = 300 + Lx
+    params = (1 / 0.8, 0.1, 1.0, 1.0)
+    st = oracle.init_constrained(Lx, Ly, seed, 0.05, 0.3)
+    with _lattice(cc, Lx, Ly, tile) as lat:
+        lat.init_constrained(seed, 0.05, 0.3)
+        for s in range(4):
+            lat.sweep(1, *params, obs_every=1)
+            st, rec = oracle_run(st, seed, s, 1, *params)
+            got = lat.get_state()
+            assert np.array_equal(got, st), (shape, tile, s, first_difference(got, st))
+        assert np.array_equal(lat.obs_series()[-1], rec[-1])
+
+
+def _near_seed(Lx, Ly, want, max_phase=320):
+    for seed in range(1, 20000):
+        for P in range(max_phase):
+            r = oracle.schedule(Lx, Ly, seed, P)[2:]
+            if r == want:
+                return seed, P
+    raise AssertionError("no seed found")
+
+
+@pytest.mark.parametrize("want", [(1, 0), (1023, 0), (0, 1), (0, 63)])
+def test_tile_path_nearest_neighbour_phases(cc, want):
+    """Phases whose offset is an exact nearest neighbour (the partner shares a
+    bond, and b's class is one of a's neighbour classes) on the tile path."""
+    Lx, Ly = 1024, 64
+    seed, P = _near_seed(Lx, Ly, want)
+    nsw = P // 8 + 1
+    params = (1.3, -0.2, 1.0, 0.7)
+    st = oracle.init_constrained(Lx, Ly, seed, 0.1, 0.4)
+    with _lattice(cc, Lx, Ly, True) as lat:
+        lat.init_constrained(seed, 0.1, 0.4)
+        lat.sweep(nsw, *params, obs_every=1)
+        st, rec = oracle_run(st, seed, 0, nsw, *params)
+        assert np.array_equal(lat.get_state(), st), (want, seed, P)
+        assert np.array_equal(lat.obs_series(), rec)
