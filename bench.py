@@ -100,6 +100,39 @@ class ClockSampler:
                 "sm_max_mhz": smax or None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def launches_per_call(nsweeps: int, obs_every: int, done: int) -> int:
+    """Kernel launches of one ccmc_sweep call, following the library's rule:
+    16-sweep (or obs_every-aligned) captured chunks when they fit, single
+    sweeps otherwise; a sweep is 8 phase kernels, each recount one kernel, each
+    chunk or single sweep ends with one counter-advance kernel."""
+    n, s = 0, 0
+    while s < nsweeps:
+        a = done + s
+        rem = nsweeps - s
+        if 0 < obs_every <= 16:
+            g = obs_every * (16 // obs_every)
+            if a % obs_every == 0 and rem >= g:
+                n += 8 * g + g // obs_every + 1
+                s += g
+                continue
+        else:
+            dist = obs_every - a % obs_every if obs_every > 0 else 1 << 60
+            if rem >= 16 and dist > 16:
+                n += 8 * 16 + 1
+                s += 16
+                continue
+        n += 8 + (1 if obs_every > 0 and (a + 1) % obs_every == 0 else 0) + 1
+        s += 1
+    return n
+
+
+def tile_ok(s) -> bool:
+    """Whether the lattice takes the tile-staged phase kernel (rows of W words
+    with W a multiple of 4 dividing 256, and Ly/4 a multiple of 256/W)."""
+    W = (s.Lx // 4 + 15) // 16
+    return (s.Lx // 4) % 16 == 0 and W % 4 == 0 and 256 % W == 0 and (s.Ly // 4) % (256 // W) == 0
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -276,8 +309,18 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    sims = temperature_sweep_4096(obs_every=STEP_SWEEPS)
-    sims = [type(s)(**{**s.__dict__, "seed": s.seed + 4 * rank}) for s in sims]
+    if args.workload == "large16384":
+        from workloads import large_16384
+
+        sims = [large_16384(obs_every=1)]
+        workload_desc = ("16384x16384 near the charge-ordering crossover (Delta=0.2, V=1, J=0.5, "
+                         "n=0.05, T=0.6), 10 sweeps per step, observables and histograms of "
+                         "M, M_stag, S_stag every sweep")
+    else:
+        sims = temperature_sweep_4096(obs_every=STEP_SWEEPS)
+        workload_desc = ("4096x4096 temperature sweep: 4 lattices (T=0.2,0.5,1,2; Delta=0, "
+                         "V=0.5, J=1, n=0.1, c=0.3), 10 sweeps each per step")
+    sims = [type(s)(**{**s.__dict__, "seed": s.seed + len(sims) * rank}) for s in sims]
     # explicit streams: one issuing stream for the timing events and the L2 flush,
     # one per lattice so that the four run concurrently (torch's default stream
     # has handle 0, which the library reads as "create your own")
@@ -286,6 +329,8 @@ def run_ours(args):
     lats = [cc.Lattice(s.Lx, s.Ly, stream=st) for s, st in zip(sims, streams)]
     for lat, s in zip(lats, sims):
         lat.init_constrained(s.seed, s.n, s.charged_frac)
+        if args.workload == "large16384":
+            lat.hist_enable(1024)
     batch = cc.Batch(lats, stream=main)
     cols = ([s.beta for s in sims], [s.Delta for s in sims], [s.V for s in sims],
             [s.J for s in sims])
@@ -297,7 +342,7 @@ def run_ours(args):
         ev0.record(main)
         for st in streams:
             st.wait_event(ev0)
-        batch.sweep(STEP_SWEEPS, *cols, obs_every=STEP_SWEEPS)
+        batch.sweep(STEP_SWEEPS, *cols, obs_every=sims[0].obs_every)
         for st in streams:
             e = torch.cuda.Event()
             e.record(st)
@@ -363,8 +408,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for lat, s, h in zip(lats, sims, host_states):
             lat.set_state_ptr(h.data_ptr(), s.seed, 0)
-        batch.sweep(STEP_SWEEPS, *cols, obs_every=STEP_SWEEPS)
-        recs = [lat.obs_series(cap=4) for lat in lats]
+        batch.sweep(STEP_SWEEPS, *cols, obs_every=sims[0].obs_every)
+        recs = [lat.obs_series(cap=16) for lat in lats]
         dt = time.perf_counter() - t0
         rec_bytes = sum(r.nbytes for r in recs)
         if k > 0:
@@ -377,22 +422,23 @@ def run_ours(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": "4096x4096 temperature sweep: 4 lattices (T=0.2,0.5,1,2; "
-                                   "Delta=0, V=0.5, J=1, n=0.1, c=0.3), 10 sweeps each per step",
+            "config": {"workload": workload_desc,
                        "lattices_per_gpu": len(sims), "sweeps_per_step": STEP_SWEEPS,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
             "clocks": clocks, "wall_s": t_wall,
-            # per step and lattice: 80 phase launches, a recount, a counter advance
-            "gpu_launches": args.steps * len(sims) * (STEP_SWEEPS * 8 + 2),
+            # per step and lattice: 80 phase launches, the recounts, counter advances
+            "gpu_launches": args.steps * len(sims) * launches_per_call(
+                STEP_SWEEPS, sims[0].obs_every, STEP_SWEEPS),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "phase_kernel (one colour phase of a 4096^2 lattice)",
+                         "kernel": f"colour phase of one {s0.Lx}^2 lattice "
+                                   f"({'phase_tile_kernel' if tile_ok(s0) else 'phase_kernel'})",
                          "peak_source": peak_kind, "launch_ms": phase_ms},
             "e2e": {"value": e2e_value, "unit": "site-updates/s",
                     "h2d_bytes_per_step": int(sum(h.numel() for h in host_states)),
                     "d2h_bytes_per_step": int(rec_bytes)},
         }
-        if not args.no_side:
+        if not args.no_side and args.workload == "temperature4096":
             line["batched"] = measure_batched(cc)
             line["served"] = measure_served(cc)
         if not args.no_cpu_baseline:
@@ -414,6 +460,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-side", action="store_true",
                     help="skip the batched-replica and served-stream measurements")
+    ap.add_argument("--workload", default="temperature4096",
+                    choices=["temperature4096", "large16384"],
+                    help="temperature4096 (default): four 4096^2 lattices; large16384: one "
+                         "16384^2 lattice with observables and histograms every sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
