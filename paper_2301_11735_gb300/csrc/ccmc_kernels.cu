@@ -89,7 +89,14 @@ struct PhaseU {
   const uint32_t *cA, *cAL, *cAR, *cAU, *cAD, *cB, *cBL, *cBR, *cBU, *cBD;
   int offAL, offAR, offB, offBL, offBR;
   int dyAU, dyAD, qy, dyBU, dyBD;
+  int wmask;  // W - 1 (rows of power-of-two width only)
 };
+
+// How phase_word reads its windows: rows of any width (kRowGeneral), rows of
+// whole words (kRowAligned), or rows of whole words and power-of-two width W,
+// staged as bands whose first row is the tile's first row (kRowTile: column
+// wraps are masks and every row offset dy is 0).
+enum RowMode { kRowGeneral = 0, kRowAligned = 1, kRowTile = 2 };
 
 __device__ __forceinline__ int wrap(int v, int n) { return v >= n ? v - n : (v < 0 ? v + n : v); }
 
@@ -120,15 +127,19 @@ __device__ __forceinline__ PhaseU phase_uniform(const Geo &g, const Sched &sc) {
   u.qy = (byy >> 2) % g.Cy;
   u.dyBU = cby == 0 ? -1 : 0;
   u.dyBD = cby == 3 ? 1 : 0;
+  u.wmask = g.W - 1;
   return u;
 }
 
 // Window of n sites at column 16 w + off (mod Cx) of one class row.
-template <bool kAligned>
-__device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, int row, int w,
-                                           int off, int n) {
+template <int kMode>
+__device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, const PhaseU &u,
+                                           int row, int w, int off, int n) {
   const uint32_t *r = cls + row * g.W;
-  if (kAligned) {  // rows are whole words: the window straddles at most two
+  if constexpr (kMode == kRowTile) {
+    const int wl = (w + (off >> 4)) & u.wmask;
+    return __funnelshift_r(r[wl], r[(wl + 1) & u.wmask], 2 * (off & 15));
+  } else if constexpr (kMode == kRowAligned) {  // the window straddles at most two words
     const int wl = wrap(w + (off >> 4), g.W);
     const int sh = 2 * (off & 15);
     if (sh == 0) return r[wl];
@@ -142,28 +153,30 @@ __device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, in
 // j: the pair's row in the class (keys the random streams); jr: the row of the
 // a word in u's arrays (j itself for the lattice in global memory, the row
 // inside a staged tile otherwise).
-template <bool kAligned>
+template <int kMode>
 __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
                                            const uint32_t *thrhi, const uint32_t *thr32, int j,
                                            int jr, int w, uint64_t P) {
+  constexpr bool kAligned = kMode != kRowGeneral;
+  // row jr + dy of a class (periodic in Cy); staged bands start at the right row
+  auto row = [&](int r0, int dy) { return kMode == kRowTile ? r0 : wrap(r0 + dy, g.Cy); };
   const int s0 = w << 4;
   const int n = kAligned ? 16 : min(16, g.Cx - s0);
-  const int Cy = g.Cy;
 
   // ---- gather: the a word, the b window and the eight neighbour windows
   uint32_t *rowA = const_cast<uint32_t *>(u.cA) + jr * g.W;
   const uint32_t A = rowA[w];
   Sums sa{0u, 0u, 0u, 0u}, sb{0u, 0u, 0u, 0u};
-  add_neighbour(sa, window<kAligned>(u.cAL, g, jr, w, u.offAL, n));
-  add_neighbour(sa, window<kAligned>(u.cAR, g, jr, w, u.offAR, n));
-  add_neighbour(sa, u.cAU[wrap(jr + u.dyAU, Cy) * g.W + w]);
-  add_neighbour(sa, u.cAD[wrap(jr + u.dyAD, Cy) * g.W + w]);
-  const int jb = wrap(jr + u.qy, Cy);
-  const uint32_t B = window<kAligned>(u.cB, g, jb, w, u.offB, n);
-  add_neighbour(sb, window<kAligned>(u.cBL, g, jb, w, u.offBL, n));
-  add_neighbour(sb, window<kAligned>(u.cBR, g, jb, w, u.offBR, n));
-  add_neighbour(sb, window<kAligned>(u.cBU, g, wrap(jb + u.dyBU, Cy), w, u.offB, n));
-  add_neighbour(sb, window<kAligned>(u.cBD, g, wrap(jb + u.dyBD, Cy), w, u.offB, n));
+  add_neighbour(sa, window<kMode>(u.cAL, g, u, jr, w, u.offAL, n));
+  add_neighbour(sa, window<kMode>(u.cAR, g, u, jr, w, u.offAR, n));
+  add_neighbour(sa, u.cAU[row(jr, u.dyAU) * g.W + w]);
+  add_neighbour(sa, u.cAD[row(jr, u.dyAD) * g.W + w]);
+  const int jb = row(jr, u.qy);
+  const uint32_t B = window<kMode>(u.cB, g, u, jb, w, u.offB, n);
+  add_neighbour(sb, window<kMode>(u.cBL, g, u, jb, w, u.offBL, n));
+  add_neighbour(sb, window<kMode>(u.cBR, g, u, jb, w, u.offBR, n));
+  add_neighbour(sb, window<kMode>(u.cBU, g, u, row(jb, u.dyBU), w, u.offB, n));
+  add_neighbour(sb, window<kMode>(u.cBD, g, u, row(jb, u.dyBD), w, u.offB, n));
 
   // ---- pair states in 4-bit lanes: lane u of pcE is site 2u, of pcO site 2u+1
   const uint32_t pcE = ((A & 0x33333333u) << 2) | (B & 0x33333333u);
@@ -284,7 +297,15 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
   if (dA) rowA[w] = A ^ dA;
   if (dB) {
     uint32_t *rb = const_cast<uint32_t *>(u.cB) + jb * g.W;
-    if (kAligned) {
+    if constexpr (kMode == kRowTile) {
+      const int wl = (w + (u.offB >> 4)) & u.wmask;
+      const int sh = 2 * (u.offB & 15);
+      atomicXor(rb + wl, dB << sh);
+      if (sh) {
+        const uint32_t hi = dB >> (32 - sh);
+        if (hi) atomicXor(rb + ((wl + 1) & u.wmask), hi);
+      }
+    } else if constexpr (kAligned) {
       const int wl = wrap(w + (u.offB >> 4), g.W);
       const int sh = 2 * (u.offB & 15);
       atomicXor(rb + wl, dB << sh);
@@ -331,7 +352,7 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *th
   int j = wid / g.W, w = wid - j * g.W;
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
-    phase_word<kAligned>(g, u, sm.trans, sm.thrhi, thr32, j, j, w, P);
+    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, thr32, j, j, w, P);
     w += sw;
     j += sj;
     if (w >= g.W) {
@@ -347,20 +368,23 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *th
 // consecutive rows of the a-class (256 words, one per thread).  One thread
 // stages the tile's ten row bands -- the a rows, the b rows and the rows of
 // all eight neighbour classes, each band R full rows -- into shared memory with
-// bulk asynchronous copies that complete on an mbarrier; two buffers let the
-// next tile's copies run while this tile is evaluated.  The per-word code then
-// reads every window from shared memory, and the a and b bands go back with
-// bulk copies.  No two tiles of a phase write the same rows (each b row is the
-// partner row of exactly one a row), so global memory sees no atomics.
+// bulk asynchronous copies that complete on an mbarrier.  Three buffers rotate:
+// while a tile is evaluated, the next one is already staged and the previous
+// one's a and b bands are going back to global memory with bulk copies, so a
+// tile costs one block barrier.  No two tiles of a phase write the same rows
+// (each b row is the partner row of exactly one a row), and no tile reads a
+// row another tile writes (the pairs of a phase do not interact), so global
+// memory sees no atomics and staging may run ahead of the write-back.
 constexpr int kTileWords = 256;
 constexpr int kBands = 10;
+constexpr int kTileBufs = 3;
 constexpr int kWaitSpins = 1 << 20;  // bounded mbarrier waits
 
 struct TileSmem {
   uint32_t thrhi[kThrHiWords];
   uint2 trans[kTransN];
-  alignas(128) uint32_t band[2][kBands][kTileWords];
-  alignas(8) unsigned long long mbar[2];
+  alignas(128) uint32_t band[kTileBufs][kBands][kTileWords];
+  alignas(8) unsigned long long mbar[kTileBufs];
   Sched sched;
   int err;
 };
@@ -411,11 +435,12 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
                                                             const uint32_t *trans_far,
                                                             const uint32_t *trans_near,
                                                             int64_t p_off) {
-  __shared__ TileSmem sm;
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem);
   for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) sm.thrhi[t] = thrhi[t];
   if (threadIdx.x == 0) {
     sm.err = 0;
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < kTileBufs; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar[b])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -457,41 +482,47 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
     }
   };
 
-  uint32_t par0 = 0u, par1 = 0u;  // phase parity of each buffer's mbarrier
-  int buf = 0;
-  int tile = blockIdx.x;
-  if (threadIdx.x == 0 && tile < ntiles) stage(tile, 0);
-  __syncthreads();
-  for (; tile < ntiles; tile += gridDim.x) {
-    const int next = tile + gridDim.x;
-    if (threadIdx.x == 0 && next < ntiles) {
-      // the other buffer's previous bulk stores must have finished reading it
-      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-      stage(next, buf ^ 1);
+  // thread 0: buffers whose copies are in flight and not yet waited for
+  unsigned staged = 0u;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 2; ++k) {
+      const int t = blockIdx.x + k * gridDim.x;
+      if (t < ntiles) {
+        stage(t, k);
+        staged |= 1u << k;
+      }
     }
-    if (!mbar_wait(smem_u32(&sm.mbar[buf]), buf ? par1 : par0)) sm.err = 1;
-    if (buf)
-      par1 ^= 1u;
-    else
-      par0 ^= 1u;
+  }
+  __syncthreads();  // the move table and the mbarrier initialisation
+
+  const int lw = __ffs(W) - 1;  // W is a power of two
+  const int jr = threadIdx.x >> lw, w = threadIdx.x & (W - 1);
+  uint32_t par = 0u;  // bit b: parity of the phase of mbar[b] waited for next
+  int buf = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const bool ok = mbar_wait(smem_u32(&sm.mbar[buf]), (par >> buf) & 1u);
+    par ^= 1u << buf;
+    if (ok) {
+      if (threadIdx.x == 0) staged &= ~(1u << buf);
+      // evaluate this thread's word from the staged bands
+      const uint32_t *base = sm.band[buf][0];
+      PhaseU lu = u;
+      lu.cA = base;
+      lu.cAL = base + 1 * kTileWords;
+      lu.cAR = base + 2 * kTileWords;
+      lu.cAU = base + 3 * kTileWords;
+      lu.cAD = base + 4 * kTileWords;
+      lu.cB = base + 5 * kTileWords;
+      lu.cBL = base + 6 * kTileWords;
+      lu.cBR = base + 7 * kTileWords;
+      lu.cBU = base + 8 * kTileWords;
+      lu.cBD = base + 9 * kTileWords;
+      phase_word<kRowTile>(g, lu, sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P);
+    } else {
+      sm.err = 1;
+    }
     __syncthreads();
     if (sm.err) break;
-    // evaluate this thread's word from the staged bands
-    PhaseU lu = u;
-    lu.cA = sm.band[buf][0];
-    lu.cAL = sm.band[buf][1];
-    lu.cAR = sm.band[buf][2];
-    lu.cAU = sm.band[buf][3];
-    lu.cAD = sm.band[buf][4];
-    lu.cB = sm.band[buf][5];
-    lu.cBL = sm.band[buf][6];
-    lu.cBR = sm.band[buf][7];
-    lu.cBU = sm.band[buf][8];
-    lu.cBD = sm.band[buf][9];
-    lu.dyAU = lu.dyAD = lu.qy = lu.dyBU = lu.dyBD = 0;
-    const int jr = threadIdx.x / W, w = threadIdx.x - jr * W;
-    phase_word<true>(g, lu, sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P);
-    __syncthreads();
     if (threadIdx.x == 0) {
       // write the a and b bands back
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -507,15 +538,24 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
         bulk_store(const_cast<uint32_t *>(u.cB), src + (uint32_t)n1 * row_bytes,
                    (uint32_t)(R - n1) * row_bytes);
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      // stage the tile after next into the buffer evaluated one tile ago, once
+      // its write-back (committed one tile ago) has read it
+      const int next2 = tile + 2 * gridDim.x;
+      if (next2 < ntiles) {
+        const int nb = buf == 0 ? kTileBufs - 1 : buf - 1;
+        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        stage(next2, nb);
+        staged |= 1u << nb;
+      }
     }
-    buf ^= 1;
+    buf = buf == kTileBufs - 1 ? 0 : buf + 1;
   }
   if (threadIdx.x == 0) {
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (sm.err) {
       // give copies still in flight a bounded chance to land before exiting
-      mbar_wait(smem_u32(&sm.mbar[0]), par0);
-      mbar_wait(smem_u32(&sm.mbar[1]), par1);
+      for (int b = 0; b < kTileBufs; ++b)
+        if (staged & (1u << b)) mbar_wait(smem_u32(&sm.mbar[b]), (par >> b) & 1u);
       g.ctl[kCtlStatus] = 1;
     }
   }
@@ -558,7 +598,8 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
   int j = wid / g.W, w = wid - j * g.W;
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
-    phase_word<kAligned>(g, u, sm.trans, sm.thrhi, J.thr32, j, j, w, P);
+    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, J.thr32, j, j, w,
+                                                      P);
     w += sw;
     j += sj;
     if (w >= g.W) {
@@ -574,7 +615,7 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
 // partials go to scratch; the last block to arrive sums them into a record,
 // appends it to the ring and the histograms, and re-arms the ticket.
 struct RecountArgs {
-  int64_t *partials;    // gridDim.x x 7 scratch
+  int64_t *partials;    // (gridDim.x * gridDim.y) x 7 scratch
   int64_t *ring;        // cap x 8 records (nullptr: latest only)
   int64_t ring_cap;
   int64_t *hist;        // 3 x nbins (nullptr: none)
@@ -588,29 +629,33 @@ __device__ __forceinline__ int64_t warp_sum(int64_t v) {
   return v;
 }
 
-// Adds the observables of class words tid, tid + nthreads, ... to c[7]
-// (Nc, BV, BJ, M, M_stag, S_sum, S_stag): popcounts of the charge and sign bit
-// planes against the right and down neighbour windows.
-__device__ __forceinline__ void count_words(const Geo &g, int64_t tid, int64_t nthreads, int c[7]) {
-  const int64_t nwords = 16 * g.cstride;
-  for (int64_t wid = tid; wid < nwords; wid += nthreads) {
-    const int cls = (int)(wid / g.cstride);
-    const int64_t rem = wid - (int64_t)cls * g.cstride;
-    const int j = (int)(rem / g.W), w = (int)(rem - (int64_t)j * g.W);
-    const int cx = cls & 3, cy = cls >> 2;
+// Adds the observables of words tid, tid + nthreads, ... of class `cls` to
+// c[7] (Nc, BV, BJ, M, M_stag, S_sum, S_stag): popcounts of the charge and
+// sign bit planes against the right and down neighbour windows.
+__device__ __forceinline__ void count_class(const Geo &g, int cls, int tid, int nthreads,
+                                            int c[7]) {
+  const int W = g.W, nw = g.Cy * W;
+  const int cx = cls & 3, cy = cls >> 2;
+  const int sgn = ((cx + cy) & 1) ? -1 : 1;
+  const uint32_t *X0 = g.words + (int64_t)cls * g.cstride;
+  const uint32_t *R0 = g.words + (int64_t)(cy * 4 + ((cx + 1) & 3)) * g.cstride;
+  const uint32_t *D0 = g.words + (int64_t)(((cy + 1) & 3) * 4 + cx) * g.cstride;
+  int wid = tid;
+  int j = wid / W, w = wid - j * W;
+  const int sj = nthreads / W, sw = nthreads - sj * W;
+  for (; wid < nw; wid += nthreads) {
     const int s0 = w << 4;
     const int n = min(16, g.Cx - s0);
     const uint32_t valid = n == 16 ? 0x55555555u : (((1u << (2 * n)) - 1u) & 0x55555555u);
-    const uint32_t X = g.words[wid];
-    const uint32_t Xr = fetch_window(row_ptr(g, cy * 4 + ((cx + 1) & 3), j), g.W, g.Cx,
+    const uint32_t X = X0[wid];
+    const uint32_t Xr = fetch_window(R0 + j * W, W, g.Cx,
                                      cx == 3 ? (s0 + 1 == g.Cx ? 0 : s0 + 1) : s0, n);
     const int jd = cy == 3 ? (j + 1 == g.Cy ? 0 : j + 1) : j;
-    const uint32_t Xd = row_ptr(g, ((cy + 1) & 3) * 4 + cx, jd)[w];
+    const uint32_t Xd = D0[jd * W + w];
     const uint32_t K = (X >> 1) & valid, G = X & valid;
     const uint32_t U = ~K & valid;  // magnetic
     const int chg = __popc(K & ~G) - __popc(K & G);
     const int mag = __popc(U & ~G) - __popc(U & G);
-    const int sgn = ((cx + cy) & 1) ? -1 : 1;
     c[0] += __popc(K);
     c[3] += mag;
     c[4] += sgn * mag;
@@ -626,15 +671,23 @@ __device__ __forceinline__ void count_words(const Geo &g, int64_t tid, int64_t n
       c[1] += __popc(KK & ~diff) - __popc(KK & diff);
       c[2] += __popc(UU & ~diff) - __popc(UU & diff);
     }
+    w += sw;
+    j += sj;
+    if (w >= W) {
+      w -= W;
+      ++j;
+    }
   }
 }
 
+// Grid (gx, 16): grid row y counts class y.
 __global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
   int c[7] = {0, 0, 0, 0, 0, 0, 0};  // Nc, BV, BJ, M, Ms, S, Ss
-  count_words(g, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
-              c);
+  count_class(g, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, c);
+  const unsigned nblocks = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
   __shared__ int64_t red[8][7];
   __shared__ bool last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -647,24 +700,36 @@ __global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
   if (threadIdx.x < 7) {
     int64_t v = 0;
     for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) v += red[wv][threadIdx.x];
-    a.partials[blockIdx.x * 7 + threadIdx.x] = v;
+    a.partials[bid * 7 + threadIdx.x] = v;
   }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned long long prev =
         atomicAdd(reinterpret_cast<unsigned long long *>(g.ctl + kCtlTicket), 1ull);
-    last = (prev == (unsigned long long)(gridDim.x - 1));
+    last = (prev == (unsigned long long)(nblocks - 1));
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the last block sums the partials with all its threads (L2 loads: the
+  // partials were written by other blocks)
   __shared__ int64_t rec[8];
+  int64_t v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] += __ldcg(a.partials + (int64_t)b * 7 + k);
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const int64_t x = warp_sum(v[k]);
+    if (lane == 0) red[warp][k] = x;
+  }
+  __syncthreads();
   if (threadIdx.x < 7) {
-    int64_t v = 0;
-    for (unsigned b = 0; b < gridDim.x; ++b)
-      v += *(volatile int64_t *)(a.partials + (int64_t)b * 7 + threadIdx.x);
-    rec[1 + threadIdx.x] = v;
+    int64_t x = 0;
+    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) x += red[wv][threadIdx.x];
+    rec[1 + threadIdx.x] = x;
   }
   if (threadIdx.x == 0) rec[0] = g.ctl[kCtlPhaseBase] / 8 + a.sweep_off;
   __syncthreads();
@@ -743,16 +808,16 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
         for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
           const int j = wid / g.W, w = wid - j * g.W;
           if (aligned)
-            phase_word<true>(gs, u, tr, s_thrhi, J.thr32, j, j, w, P);
+            phase_word<kRowAligned>(gs, u, tr, s_thrhi, J.thr32, j, j, w, P);
           else
-            phase_word<false>(gs, u, tr, s_thrhi, J.thr32, j, j, w, P);
+            phase_word<kRowGeneral>(gs, u, tr, s_thrhi, J.thr32, j, j, w, P);
         }
         __syncthreads();
       }
       const int64_t done = P0 / 8 + s + 1;
       if (obs_every > 0 && done % obs_every == 0) {
         int c[7] = {0, 0, 0, 0, 0, 0, 0};
-        count_words(gs, threadIdx.x, blockDim.x, c);
+        for (int cls = 0; cls < 16; ++cls) count_class(gs, cls, threadIdx.x, blockDim.x, c);
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
           const int64_t v = warp_sum((int64_t)c[k]);
@@ -867,12 +932,12 @@ __global__ void philox_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
 // the previous kernel of the stream drains, and waits for it (griddepcontrol)
 // before touching anything that kernel writes.
 template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s,
-                              Args... args) {
+static cudaError_t launch_pdl_smem(void (*kernel)(KArgs...), dim3 grid, int block, size_t smem,
+                                   cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)grid);
+  cfg.gridDim = grid;
   cfg.blockDim = dim3((unsigned)block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -880,6 +945,12 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cud
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int block, cudaStream_t s,
+                              Args... args) {
+  return launch_pdl_smem(kernel, grid, block, 0, s, args...);
 }
 
 static int grid_for(int64_t items, int block, int cap) {
@@ -909,14 +980,21 @@ bool tile_path_ok(const Geo &g) {
          g.Cy % (kTileWords / g.W) == 0;
 }
 
+// Also raises the tile kernel's dynamic shared memory limit on the current
+// device (outside any stream capture: called when a lattice is created).  0
+// when that fails: the lattice then takes the direct path.
 int tile_resident_grid() {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel, 256, 0) !=
-          cudaSuccess ||
-      per_sm < 1 || sms < 1)
-    return 152 * 2;
+  if (cudaFuncSetAttribute(phase_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(TileSmem)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel, 256,
+                                                    sizeof(TileSmem)) != cudaSuccess ||
+      per_sm < 1 || sms < 1) {
+    cudaGetLastError();
+    return 0;
+  }
   return per_sm * sms;
 }
 
@@ -926,8 +1004,8 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
   if (cfg.tile_grid > 0) {
     const int64_t tiles = nw / kTileWords;
     const int grid = (int)(tiles < cfg.tile_grid ? tiles : cfg.tile_grid);
-    return launch_pdl(phase_tile_kernel, grid, 256, s, g, t.thrhi, t.thr32, t.trans_far,
-                      t.trans_near, p_off);
+    return launch_pdl_smem(phase_tile_kernel, grid, 256, sizeof(TileSmem), s, g, t.thrhi,
+                           t.thr32, t.trans_far, t.trans_near, p_off);
   }
   const int grid = grid_for(nw, 256, cfg.phase_grid_cap);
   const uint32_t *thrhi = t.thrhi, *thr32 = t.thr32, *tf = t.trans_far, *tn = t.trans_near;
@@ -942,12 +1020,16 @@ cudaError_t launch_phase_multi(const MultiJob *d_jobs, int njobs, int grid, bool
   return launch_pdl(phase_multi_kernel<false>, grid, 256, s, d_jobs, njobs, p_off);
 }
 
-int recount_grid(const Geo &g) { return grid_for(16 * g.cstride, 256, 152 * 4); }
+// Grid x-extent of recount_kernel (its y-extent is the 16 classes): at most
+// 16 x 57 = 912 blocks, six per SM at 40 registers a thread.
+static int recount_gx(const Geo &g) { return grid_for((int64_t)g.Cy * g.W, 256, 57); }
+
+int recount_grid(const Geo &g) { return 16 * recount_gx(g); }
 
 cudaError_t launch_recount(const Geo &g, int64_t *partials, int64_t *ring, int64_t ring_cap,
                            int64_t *hist, int nbins, int64_t sweep_off, cudaStream_t s) {
   RecountArgs a{partials, ring, ring_cap, hist, nbins, sweep_off};
-  return launch_pdl(recount_kernel, recount_grid(g), 256, s, g, a);
+  return launch_pdl(recount_kernel, dim3((unsigned)recount_gx(g), 16u), 256, s, g, a);
 }
 
 cudaError_t launch_advance(int64_t *ctl, int64_t phases, cudaStream_t s) {
