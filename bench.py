@@ -140,20 +140,31 @@ def _dist():
     return world, rank, local
 
 
+def workload(name: str):
+    """(sims, description) of a named bench workload."""
+    from workloads import large_16384, temperature_sweep_4096
+
+    if name == "large16384":
+        return [large_16384(obs_every=1)], (
+            "16384x16384 near the charge-ordering crossover (Delta=0.2, V=1, J=0.5, n=0.05, "
+            "T=0.6), 10 sweeps per step, observables and histograms of M, M_stag, S_stag every "
+            "sweep")
+    return temperature_sweep_4096(obs_every=STEP_SWEEPS), (
+        "4096x4096 temperature sweep: 4 lattices (T=0.2,0.5,1,2; Delta=0, V=0.5, J=1, n=0.1, "
+        "c=0.3), 10 sweeps each per step")
+
+
 def run_reference(args):
     """The CPU oracle on a bounded sample of the workload (rank 0 only)."""
     world, rank, _ = _dist()
     if rank != 0:
         return
-    import numpy as np
-
     import oracle
-    from workloads import temperature_sweep_4096
 
-    sims = temperature_sweep_4096(obs_every=STEP_SWEEPS)
-    # bounded sample: the first `sweeps` sweeps of one lattice per step, all
-    # four temperatures visited in turn
-    sample_sweeps = 2
+    sims, desc = workload(args.workload)
+    # bounded sample: the first sweeps of one lattice per step (recounts at the
+    # workload's observable interval included), the lattices visited in turn
+    sample_sweeps = 1 if sims[0].sites > (1 << 26) else 2
     states = {}
     for s in sims:
         states[s.seed] = oracle.init_constrained(s.Lx, s.Ly, s.seed, s.n, s.charged_frac)
@@ -163,7 +174,7 @@ def run_reference(args):
         s = sims[k % len(sims)]
         t0 = time.perf_counter()
         oracle.sweeps(states[s.seed], s.seed, done[s.seed], sample_sweeps, s.beta, s.Delta, s.V,
-                      s.J, obs_every=0)
+                      s.J, obs_every=s.obs_every)
         dt = time.perf_counter() - t0
         done[s.seed] += sample_sweeps
         if k >= args.warmup:
@@ -175,11 +186,10 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "4096x4096 temperature sweep (T=0.2,0.5,1,2; Delta=0, V=0.5, J=1,"
-                               " n=0.1, c=0.3)", "sample_per_step": f"{sample_sweeps} sweeps of one "
-                               "4096^2 lattice"},
+        "config": {"workload": desc, "sample_per_step": f"{sample_sweeps} sweeps of one "
+                                                        f"{s.Lx}^2 lattice"},
         "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample_sweeps} sweeps of one 4096^2 lattice per step, "
+                         "sample": f"{sample_sweeps} sweeps of one {s.Lx}^2 lattice per step, "
                                    f"{args.steps} steps"},
         "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -187,22 +197,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample(target_s: float = 12.0):
-    """Time the oracle (single-threaded C, as it stands) on whole sweeps of the
-    first 4096^2 lattice of the workload until about target_s seconds pass."""
+def cpu_baseline_sample(sims, target_s: float = 12.0):
+    """Time the oracle (single-threaded C, as it stands) on whole sweeps of one
+    lattice of the workload (the second if there are several), with the
+    workload's observable interval, until about target_s seconds pass."""
     import oracle
-    from workloads import temperature_sweep_4096
 
-    s = temperature_sweep_4096()[1]
+    s = sims[1 if len(sims) > 1 else 0]
     st = oracle.init_constrained(s.Lx, s.Ly, s.seed, s.n, s.charged_frac)
     t0 = time.perf_counter()
     n = 0
     while time.perf_counter() - t0 < target_s:
-        oracle.sweeps(st, s.seed, n, 1, s.beta, s.Delta, s.V, s.J, obs_every=0)
+        oracle.sweeps(st, s.seed, n, 1, s.beta, s.Delta, s.V, s.J,
+                      obs_every=1 if s.obs_every == 1 else 0)
         n += 1
     dt = time.perf_counter() - t0
     return {"value": s.sites * n / dt, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} sweeps of the 4096^2 lattice at T={s.T} ({dt:.1f} s, 1 thread)"}
+            "sample": f"{n} sweeps of one {s.Lx}^2 lattice of the workload at T={s.T} "
+                      f"({dt:.1f} s, 1 thread)"}
 
 
 def measure_batched(cc, nsweeps=5000, plain_sample=32, plain_sweeps=200):
@@ -300,7 +312,6 @@ def run_ours(args):
     import torch
 
     import paper_2301_11735_gb300 as cc
-    from workloads import temperature_sweep_4096
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -309,17 +320,7 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if args.workload == "large16384":
-        from workloads import large_16384
-
-        sims = [large_16384(obs_every=1)]
-        workload_desc = ("16384x16384 near the charge-ordering crossover (Delta=0.2, V=1, J=0.5, "
-                         "n=0.05, T=0.6), 10 sweeps per step, observables and histograms of "
-                         "M, M_stag, S_stag every sweep")
-    else:
-        sims = temperature_sweep_4096(obs_every=STEP_SWEEPS)
-        workload_desc = ("4096x4096 temperature sweep: 4 lattices (T=0.2,0.5,1,2; Delta=0, "
-                         "V=0.5, J=1, n=0.1, c=0.3), 10 sweeps each per step")
+    sims, workload_desc = workload(args.workload)
     sims = [type(s)(**{**s.__dict__, "seed": s.seed + len(sims) * rank}) for s in sims]
     # explicit streams: one issuing stream for the timing events and the L2 flush,
     # one per lattice so that the four run concurrently (torch's default stream
@@ -442,7 +443,7 @@ def run_ours(args):
             line["batched"] = measure_batched(cc)
             line["served"] = measure_served(cc)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline_sample()
+            line["cpu_baseline"] = cpu_baseline_sample(sims)
         print(json.dumps(line), flush=True)
     batch.close()
     for lat in lats:
