@@ -27,6 +27,7 @@ of the same workload.  Under torchrun each rank runs its own four lattices
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -39,6 +40,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 STEP_SWEEPS = 10
+
+# Counters of one phase launch of the bench's dominant kernel, from the ncu
+# captures summarised in profiles/phase_tile_kernel_<workload>.md:
+# dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum.
+# They hold only for the kernel sources they were taken with (KERNEL_DIGEST);
+# after any change to those sources the bench reports them as null.
+PHASE_COUNTERS = {
+    "large16384": {"digest": "6253d8aaf55faddb67b610114cdaf681b9815a23b3a204c8940d7f27444bf983",
+                   "traffic": 33_645_568, "warp_inst": 32_680_572},
+}
+KERNEL_SOURCES = ("ccmc_kernels.cu", "ccmc_device.cuh", "ccmc_internal.h")
+
+
+def kernel_digest() -> str:
+    """sha256 over the phase kernel's source files, in KERNEL_SOURCES order."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2301_11735_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def _peaks():
@@ -396,6 +417,18 @@ def run_ours(args):
     alg_bytes = 1.5 * s0.sites / 8
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (phase_ms * 1e-3) / 1e9
+    counters = PHASE_COUNTERS.get(args.workload)
+    if counters and counters["digest"] != kernel_digest():
+        counters = None  # the kernel changed since the capture
+    issue = None
+    if counters:
+        # warp-instructions per second against one per scheduler per cycle
+        # (4 schedulers per SM) at the maximum SM clock
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_issue = 4 * sms * float(clocks.get("sm_max_mhz") or 2070.0) * 1e6
+        rate = counters["warp_inst"] / (phase_ms * 1e-3)
+        issue = {"warp_inst_per_launch": counters["warp_inst"], "achieved": rate,
+                 "peak": peak_issue, "unit": "warp-inst/s", "frac": rate / peak_issue}
 
     # end to end through the C ABI with host buffers
     host_states = []
@@ -431,7 +464,9 @@ def run_ours(args):
             "gpu_launches": args.steps * len(sims) * launches_per_call(
                 STEP_SWEEPS, sims[0].obs_every, STEP_SWEEPS),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": counters["traffic"] if counters else None,
+                         "issue": issue,
                          "kernel": f"colour phase of one {s0.Lx}^2 lattice "
                                    f"({'phase_tile_kernel' if tile_ok(s0) else 'phase_kernel'})",
                          "peak_source": peak_kind, "launch_ms": phase_ms},
