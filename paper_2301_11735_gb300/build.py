@@ -1,9 +1,10 @@
 """Build ``libccmc.so`` in-tree (``paper_2301_11735_gb300/_build``) for sm_103a.
 
-Five translation units are compiled in parallel and linked into one shared
+Six translation units are compiled in parallel and linked into one shared
 library that exports the C ABI of ``include/ccmc.h``:
 
-* ``csrc/ccmc_kernels.cu`` -- the CUDA kernels (nvcc, sm_103a only);
+* ``csrc/ccmc_phase.cu``   -- the colour-phase kernels (nvcc, sm_103a only);
+* ``csrc/ccmc_kernels.cu`` -- the other CUDA kernels (init, recount, packing);
 * ``csrc/ccmc_api.cu``     -- host code of the C ABI (nvcc host pass);
 * ``csrc/ccmc_noalloc.cu`` -- the recount entry point that allocates nothing;
 * ``csrc/ccmc_tables.cpp`` -- FP64 threshold tables (g++);
@@ -61,6 +62,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if ptxas_verbose:
         common += ["-Xptxas", "-v"]
     jobs = {
+        "ccmc_phase.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_phase.cu")],
         "ccmc_kernels.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_kernels.cu")],
         "ccmc_api.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_api.cu")],
         "ccmc_noalloc.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_noalloc.cu")],

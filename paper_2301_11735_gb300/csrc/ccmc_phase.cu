@@ -1,0 +1,734 @@
+// ccmc_phase.cu -- the colour-phase kernels of the coupled-pair Metropolis
+// sweep for sm_103a (one lattice per launch: direct and tile-staged; several
+// lattices in lock step; the resident batch kernel) and their launchers
+// (declared in ccmc_internal.h).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ccmc_count.cuh"
+#include "ccmc_device.cuh"
+#include "ccmc_internal.h"
+#include "ccmc_launch.cuh"
+
+namespace ccmc {
+
+// ============================================================================
+// One colour phase (Sec. 3.1-3.2).  Each thread owns one word of the a-class:
+// up to 16 pairs (a, a + r).  It reads the a word, the four neighbour windows
+// of a, the b window and the four neighbour windows of b; evaluates every
+// pair's move; stores the a word and XORs the changed b sites back.
+//
+// Per pair, with pc = 4 code_a + code_b and its 32-bit random word R (16-bit
+// choice v in the low half, top half u of the acceptance word in the high):
+//   entry  = trans[pc][v mod 12]  -> base, byte coefficients, pc XOR npc
+//   index  = dp4a(coefficients, (D8, GA, GB, 0), base)  (threshold index)
+//   accept = R < thrhi[index], i.e. u < the threshold's top half (v < 2^16)
+// The fast decision is always applied.  A tie of the top halves, or a choice
+// field v >= 65532, marks the pair rare: the exact path then undoes the fast
+// decision and applies the exact one with the pair's SLOW random words
+// (about one pair in 10^4).
+struct PhaseSmem {
+  uint2 trans[kTransN];
+  uint32_t thrhi[kThrHiWords];
+  Sched sched;
+};
+
+// Uniform per phase: where the ten windows of a word come from.  Column offsets
+// are in sites, normalised to [0, Cx).
+struct PhaseU {
+  const uint32_t *cA, *cAL, *cAR, *cAU, *cAD, *cB, *cBL, *cBR, *cBU, *cBD;
+  int offAL, offAR, offB, offBL, offBR;
+  int dyAU, dyAD, qy, dyBU, dyBD;
+  int wmask;  // W - 1 (rows of power-of-two width only)
+};
+
+// How phase_word reads its windows: rows of any width (kRowGeneral), rows of
+// whole words (kRowAligned), or rows of whole words and power-of-two width W,
+// staged as bands whose first row is the tile's first row (kRowTile: column
+// wraps are masks and every row offset dy is 0).
+enum RowMode { kRowGeneral = 0, kRowAligned = 1, kRowTile = 2 };
+
+__device__ __forceinline__ int wrap(int v, int n) { return v >= n ? v - n : (v < 0 ? v + n : v); }
+
+__device__ __forceinline__ PhaseU phase_uniform(const Geo &g, const Sched &sc) {
+  PhaseU u;
+  const int ax = sc.a0x, ay = sc.a0y;
+  const int bxx = ax + sc.rx, byy = ay + sc.ry;
+  const int cbx = bxx & 3, cby = byy & 3;
+  auto cls = [&](int cx, int cy) { return g.words + (int64_t)(cy * 4 + cx) * g.cstride; };
+  u.cA = cls(ax, ay);
+  u.cAL = cls((ax + 3) & 3, ay);
+  u.cAR = cls((ax + 1) & 3, ay);
+  u.cAU = cls(ax, (ay + 3) & 3);
+  u.cAD = cls(ax, (ay + 1) & 3);
+  u.cB = cls(cbx, cby);
+  u.cBL = cls((cbx + 3) & 3, cby);
+  u.cBR = cls((cbx + 1) & 3, cby);
+  u.cBU = cls(cbx, (cby + 3) & 3);
+  u.cBD = cls(cbx, (cby + 1) & 3);
+  const int qx = (bxx >> 2) % g.Cx;
+  u.offAL = ax == 0 ? g.Cx - 1 : 0;
+  u.offAR = ax == 3 ? (g.Cx == 1 ? 0 : 1) : 0;
+  u.offB = qx;
+  u.offBL = cbx == 0 ? wrap(qx - 1, g.Cx) : qx;
+  u.offBR = cbx == 3 ? wrap(qx + 1, g.Cx) : qx;
+  u.dyAU = ay == 0 ? -1 : 0;
+  u.dyAD = ay == 3 ? 1 : 0;
+  u.qy = (byy >> 2) % g.Cy;
+  u.dyBU = cby == 0 ? -1 : 0;
+  u.dyBD = cby == 3 ? 1 : 0;
+  u.wmask = g.W - 1;
+  return u;
+}
+
+// Window of n sites at column 16 w + off (mod Cx) of one class row.
+template <int kMode>
+__device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, const PhaseU &u,
+                                           int row, int w, int off, int n) {
+  const uint32_t *r = cls + row * g.W;
+  if constexpr (kMode == kRowTile) {
+    const int wl = (w + (off >> 4)) & u.wmask;
+    return __funnelshift_r(r[wl], r[(wl + 1) & u.wmask], 2 * (off & 15));
+  } else if constexpr (kMode == kRowAligned) {  // the window straddles at most two words
+    const int wl = wrap(w + (off >> 4), g.W);
+    const int sh = 2 * (off & 15);
+    if (sh == 0) return r[wl];
+    const int wh = wl + 1 == g.W ? 0 : wl + 1;
+    return __funnelshift_r(r[wl], r[wh], sh);
+  } else {
+    return fetch_window(r, g.W, g.Cx, wrap(16 * w + off, g.Cx), n);
+  }
+}
+
+// j: the pair's row in the class (keys the random streams); jr: the row of the
+// a word in u's arrays (j itself for the lattice in global memory, the row
+// inside a staged tile otherwise).
+template <int kMode>
+__device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
+                                           const uint32_t *thrhi, const uint32_t *thr32, int j,
+                                           int jr, int w, uint64_t P) {
+  constexpr bool kAligned = kMode != kRowGeneral;
+  // row jr + dy of a class (periodic in Cy); staged bands start at the right row
+  auto row = [&](int r0, int dy) { return kMode == kRowTile ? r0 : wrap(r0 + dy, g.Cy); };
+  const int s0 = w << 4;
+  const int n = kAligned ? 16 : min(16, g.Cx - s0);
+
+  // ---- gather: the a word, the b window and the eight neighbour windows
+  uint32_t *rowA = const_cast<uint32_t *>(u.cA) + jr * g.W;
+  const uint32_t A = rowA[w];
+  Sums sa{0u, 0u, 0u, 0u}, sb{0u, 0u, 0u, 0u};
+  add_neighbour(sa, window<kMode>(u.cAL, g, u, jr, w, u.offAL, n));
+  add_neighbour(sa, window<kMode>(u.cAR, g, u, jr, w, u.offAR, n));
+  add_neighbour(sa, u.cAU[row(jr, u.dyAU) * g.W + w]);
+  add_neighbour(sa, u.cAD[row(jr, u.dyAD) * g.W + w]);
+  const int jb = row(jr, u.qy);
+  const uint32_t B = window<kMode>(u.cB, g, u, jb, w, u.offB, n);
+  add_neighbour(sb, window<kMode>(u.cBL, g, u, jb, w, u.offBL, n));
+  add_neighbour(sb, window<kMode>(u.cBR, g, u, jb, w, u.offBR, n));
+  add_neighbour(sb, window<kMode>(u.cBU, g, u, row(jb, u.dyBU), w, u.offB, n));
+  add_neighbour(sb, window<kMode>(u.cBD, g, u, row(jb, u.dyBD), w, u.offB, n));
+
+  // ---- pair states in 4-bit lanes: lane u of pcE is site 2u, of pcO site 2u+1
+  const uint32_t pcE = ((A & 0x33333333u) << 2) | (B & 0x33333333u);
+  const uint32_t pcO = (A & 0xCCCCCCCCu) | ((B >> 2) & 0x33333333u);
+
+  // ---- byte lanes of group k (sites k, k+4, k+8, k+12): D8 = SA - SB + 8, GA, GB
+  uint32_t x01[4], x23[4], gbk[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t d8 = group_bytes(sa.se, sa.so, k) + 0x08080808u - group_bytes(sb.se, sb.so, k);
+    const uint32_t ga = group_bytes(sa.ge, sa.go, k);
+    gbk[k] = group_bytes(sb.ge, sb.go, k);
+    x01[k] = prmt(d8, ga, 0x5140u);
+    x23[k] = prmt(d8, ga, 0x7362u);
+  }
+
+  // ---- random words: pair (i, j) of the class takes word i mod 4 of
+  // Philox(seed, (j Cx4 + i / 4, P_lo, P_hi, MOVE)); call b covers pairs 4b..4b+3
+  const uint32_t gbase = (uint32_t)j * (uint32_t)g.Cx4 + (uint32_t)(4 * w);
+  uint32_t dE = 0u, dO = 0u, slow = 0u;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    if (!kAligned && 4 * b >= n) break;
+    const U4 r = philox(gbase + (uint32_t)b, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0,
+                        g.k1);
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;  // smallest R ^ TH and largest v of the group
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int t = 4 * b + k;
+      if (!kAligned && t >= n) continue;
+      const uint32_t R = k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w;
+      const uint32_t env = b == 0 ? prmt(x01[k], gbk[k], 0x8410u)
+                         : b == 1 ? prmt(x01[k], gbk[k], 0x8532u)
+                         : b == 2 ? prmt(x23[k], gbk[k], 0x8610u)
+                                  : prmt(x23[k], gbk[k], 0x8732u);
+      const uint32_t pc = (((t & 1) ? pcO : pcE) >> (4 * (t >> 1))) & 15u;
+      const uint32_t v = R & 0xFFFFu;
+      const uint32_t r12 = v - 12u * ((v * 43691u) >> 19);  // v mod 12 for v < 2^16
+      const uint2 e = trans[pc * 12u + r12];
+      const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
+      const uint32_t TH = thrhi[idx];
+      mn = min(mn, R ^ TH);
+      mx = max(mx, v);
+      // move bits of this pair (e.y bits 24-27) added at its 4-bit lane
+      const uint32_t xm = (e.y >> 24) * (1u << (4 * (t >> 1)));
+      if (t & 1)
+        dO += R < TH ? xm : 0u;
+      else
+        dE += R < TH ? xm : 0u;
+    }
+    // a tie of the top halves (R ^ TH < 2^16) or a choice field >= 65532 makes
+    // the group's pairs go through the exact path
+    if (mn < 0x10000u || mx >= 65532u) slow |= 0xFu << (4 * b);
+  }
+  uint32_t dA = ((dE >> 2) & 0x33333333u) | (((dO >> 2) & 0x33333333u) << 2);
+  uint32_t dB = (dE & 0x33333333u) | ((dO & 0x33333333u) << 2);
+
+  // ---- exact path for the flagged groups: for each truly rare pair, undo the
+  // fast decision and apply the exact one
+  U4 mv{0u, 0u, 0u, 0u};
+  int mv_group = -1;
+  while (slow) {
+    const int t = __ffs(slow) - 1;
+    slow &= slow - 1u;
+    if (!kAligned && t >= n) continue;
+    if ((t >> 2) != mv_group) {
+      mv_group = t >> 2;
+      mv = philox(gbase + (uint32_t)mv_group, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0,
+                  g.k1);
+    }
+    const int qw = t & 3;
+    const uint32_t R = qw == 0 ? mv.x : qw == 1 ? mv.y : qw == 2 ? mv.z : mv.w;
+    const uint32_t pc = (((A >> (2 * t)) & 3u) << 2) | ((B >> (2 * t)) & 3u);
+    const uint32_t v = R & 0xFFFFu, uh = R >> 16;
+    const int sh = 4 * (t >> 1);
+    const uint32_t sa4 = (((t & 1) ? sa.so : sa.se) >> sh) & 15u;
+    const uint32_t sb4 = (((t & 1) ? sb.so : sb.se) >> sh) & 15u;
+    const uint32_t ga4 = (((t & 1) ? sa.go : sa.ge) >> sh) & 15u;
+    const uint32_t gb4 = (((t & 1) ? sb.go : sb.ge) >> sh) & 15u;
+    const uint32_t env = (sa4 + 8u - sb4) | (ga4 << 8) | (gb4 << 16);
+    // the fast path's decision for this pair
+    const uint2 ef = trans[pc * 12u + v % 12u];
+    const uint32_t THf = thrhi[__dp4a((int)ef.y, (int)env, (int)ef.x)];
+    if ((R ^ THf) >= 0x10000u && v < 65532u) continue;  // not rare: the fast decision stands
+    if (R < THf) {  // undo it
+      const uint32_t x = ef.y >> 24;
+      dA ^= (x >> 2) << (2 * t);
+      dB ^= (x & 3u) << (2 * t);
+    }
+    const uint64_t kk = (uint64_t)j * g.Cx + s0 + t;
+    const U4 sl = philox((uint32_t)kk, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, g.k0, g.k1);
+    uint32_t r;
+    if (v < 65532u)
+      r = v % 12u;
+    else if (sl.y < 4294967292u)
+      r = sl.y % 12u;
+    else
+      continue;  // keep the current configuration
+    const uint2 e = trans[pc * 12u + r];
+    const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
+    const uint32_t thr = thr32[idx];
+    const uint32_t uu = (uh << 16) | (sl.x & 0xFFFFu);
+    if (thr == 0xFFFFFFFFu || uu < thr) {
+      const uint32_t x = e.y >> 24;
+      dA ^= (x >> 2) << (2 * t);
+      dB ^= (x & 3u) << (2 * t);
+    }
+  }
+  if constexpr (!kAligned) {
+    if (n < 16) {
+      const uint32_t valid = (1u << (2 * n)) - 1u;
+      dA &= valid;
+      dB &= valid;
+    }
+  }
+
+  // ---- write back: the a word is this thread's alone; the b sites share words
+  if (dA) rowA[w] = A ^ dA;
+  if (dB) {
+    uint32_t *rb = const_cast<uint32_t *>(u.cB) + jb * g.W;
+    if constexpr (kMode == kRowTile) {
+      const int wl = (w + (u.offB >> 4)) & u.wmask;
+      const int sh = 2 * (u.offB & 15);
+      atomicXor(rb + wl, dB << sh);
+      if (sh) {
+        const uint32_t hi = dB >> (32 - sh);
+        if (hi) atomicXor(rb + ((wl + 1) & u.wmask), hi);
+      }
+    } else if constexpr (kAligned) {
+      const int wl = wrap(w + (u.offB >> 4), g.W);
+      const int sh = 2 * (u.offB & 15);
+      atomicXor(rb + wl, dB << sh);
+      if (sh) {
+        const uint32_t hi = dB >> (32 - sh);
+        if (hi) atomicXor(rb + (wl + 1 == g.W ? 0 : wl + 1), hi);
+      }
+    } else {
+      scatter_xor(rb, g.Cx, wrap(s0 + u.offB, g.Cx), n, dB);
+    }
+  }
+}
+
+template <bool kAligned>
+__global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *thrhi,
+                                                    const uint32_t *thr32,
+                                                    const uint32_t *trans_far,
+                                                    const uint32_t *trans_near, int64_t p_off) {
+  __shared__ PhaseSmem sm;
+  // The tables come from host uploads that precede the whole launch chain, so
+  // they are loaded before waiting for the previous kernel of the stream (which
+  // lets this prologue overlap its tail under programmatic dependent launch).
+  for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) sm.thrhi[t] = thrhi[t];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // The next kernel may launch now: with one resident wave its blocks only take
+  // the slots of blocks that finish, and it waits for this whole grid before
+  // touching the lattice.
+  asm volatile("griddepcontrol.launch_dependents;");
+  const uint64_t P = (uint64_t)(g.ctl[kCtlPhaseBase] + p_off);
+  if (threadIdx.x < 32) {
+    const Sched s = draw_schedule(g, P);
+    if (threadIdx.x == 0) sm.sched = s;
+  }
+  __syncthreads();
+  const Sched sc = sm.sched;
+  const uint32_t *trans = sc.near ? trans_near : trans_far;
+  for (int t = threadIdx.x; t < kTransN; t += blockDim.x)
+    sm.trans[t] = make_uint2(trans[2 * t], trans[2 * t + 1]);
+  __syncthreads();
+  const PhaseU u = phase_uniform(g, sc);
+  const int nw = g.Cy * g.W;
+  int wid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  int j = wid / g.W, w = wid - j * g.W;
+  const int sj = stride / g.W, sw = stride - sj * g.W;
+  for (; wid < nw; wid += stride) {
+    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, thr32, j, j, w, P);
+    w += sw;
+    j += sj;
+    if (w >= g.W) {
+      w -= g.W;
+      ++j;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Tile-staged phase (lattices whose class rows are W words with W dividing 256
+// and a multiple of 4, and Cy a multiple of R = 256 / W).  A tile is R
+// consecutive rows of the a-class (256 words, one per thread).  One thread
+// stages the tile's ten row bands -- the a rows, the b rows and the rows of
+// all eight neighbour classes, each band R full rows -- into shared memory with
+// bulk asynchronous copies that complete on an mbarrier.  Three buffers rotate:
+// while a tile is evaluated, the next one is already staged and the previous
+// one's a and b bands are going back to global memory with bulk copies, so a
+// tile costs one block barrier.  No two tiles of a phase write the same rows
+// (each b row is the partner row of exactly one a row), and no tile reads a
+// row another tile writes (the pairs of a phase do not interact), so global
+// memory sees no atomics and staging may run ahead of the write-back.
+constexpr int kTileWords = 256;
+constexpr int kBands = 10;
+constexpr int kTileBufs = 3;
+constexpr int kWaitSpins = 1 << 20;  // bounded mbarrier waits
+
+struct TileSmem {
+  uint32_t thrhi[kThrHiWords];
+  uint2 trans[kTransN];
+  alignas(128) uint32_t band[kTileBufs][kBands][kTileWords];
+  alignas(8) unsigned long long mbar[kTileBufs];
+  Sched sched;
+  int err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kWaitSpins; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      :
+      : "r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void *dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+               :
+               : "l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+
+// Row band: R rows of one class starting at row r0 (periodic in Cy).
+struct Band {
+  const uint32_t *cls;
+  int dy;  // first row relative to the tile's first a row
+};
+
+__global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_t *thrhi,
+                                                            const uint32_t *thr32,
+                                                            const uint32_t *trans_far,
+                                                            const uint32_t *trans_near,
+                                                            int64_t p_off) {
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem);
+  for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) sm.thrhi[t] = thrhi[t];
+  if (threadIdx.x == 0) {
+    sm.err = 0;
+    for (int b = 0; b < kTileBufs; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar[b])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+  const uint64_t P = (uint64_t)(g.ctl[kCtlPhaseBase] + p_off);
+  if (threadIdx.x < 32) {
+    const Sched sc = draw_schedule(g, P);
+    if (threadIdx.x == 0) sm.sched = sc;
+  }
+  __syncthreads();
+  const Sched sc = sm.sched;
+  const uint32_t *trans = sc.near ? trans_near : trans_far;
+  for (int t = threadIdx.x; t < kTransN; t += blockDim.x)
+    sm.trans[t] = make_uint2(trans[2 * t], trans[2 * t + 1]);
+  const PhaseU u = phase_uniform(g, sc);
+  const int W = g.W, R = kTileWords / W, Cy = g.Cy;
+  const Band bands[kBands] = {{u.cA, 0},          {u.cAL, 0},          {u.cAR, 0},
+                              {u.cAU, u.dyAU},    {u.cAD, u.dyAD},     {u.cB, u.qy},
+                              {u.cBL, u.qy},      {u.cBR, u.qy},       {u.cBU, u.qy + u.dyBU},
+                              {u.cBD, u.qy + u.dyBD}};
+  const int ntiles = Cy / R;
+  const uint32_t row_bytes = (uint32_t)W * 4u;
+
+  // thread 0 stages tile `tile` into buffer `buf`
+  auto stage = [&](int tile, int buf) {
+    const uint32_t bar = smem_u32(&sm.mbar[buf]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((uint32_t)(kBands * kTileWords * 4))
+                 : "memory");
+    const int j0 = tile * R;
+    for (int k = 0; k < kBands; ++k) {
+      int r0 = (j0 + bands[k].dy) % Cy;
+      if (r0 < 0) r0 += Cy;
+      const int n1 = min(R, Cy - r0);
+      const uint32_t dst = smem_u32(&sm.band[buf][k][0]);
+      bulk_load(dst, bands[k].cls + (int64_t)r0 * W, (uint32_t)n1 * row_bytes, bar);
+      if (n1 < R) bulk_load(dst + (uint32_t)n1 * row_bytes, bands[k].cls, (uint32_t)(R - n1) * row_bytes, bar);
+    }
+  };
+
+  // thread 0: buffers whose copies are in flight and not yet waited for
+  unsigned staged = 0u;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 2; ++k) {
+      const int t = blockIdx.x + k * gridDim.x;
+      if (t < ntiles) {
+        stage(t, k);
+        staged |= 1u << k;
+      }
+    }
+  }
+  __syncthreads();  // the move table and the mbarrier initialisation
+
+  const int lw = __ffs(W) - 1;  // W is a power of two
+  const int jr = threadIdx.x >> lw, w = threadIdx.x & (W - 1);
+  uint32_t par = 0u;  // bit b: parity of the phase of mbar[b] waited for next
+  int buf = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const bool ok = mbar_wait(smem_u32(&sm.mbar[buf]), (par >> buf) & 1u);
+    par ^= 1u << buf;
+    if (ok) {
+      if (threadIdx.x == 0) staged &= ~(1u << buf);
+      // evaluate this thread's word from the staged bands
+      const uint32_t *base = sm.band[buf][0];
+      PhaseU lu = u;
+      lu.cA = base;
+      lu.cAL = base + 1 * kTileWords;
+      lu.cAR = base + 2 * kTileWords;
+      lu.cAU = base + 3 * kTileWords;
+      lu.cAD = base + 4 * kTileWords;
+      lu.cB = base + 5 * kTileWords;
+      lu.cBL = base + 6 * kTileWords;
+      lu.cBR = base + 7 * kTileWords;
+      lu.cBU = base + 8 * kTileWords;
+      lu.cBD = base + 9 * kTileWords;
+      phase_word<kRowTile>(g, lu, sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P);
+    } else {
+      sm.err = 1;
+    }
+    __syncthreads();
+    if (sm.err) break;
+    if (threadIdx.x == 0) {
+      // write the a and b bands back
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const int j0 = tile * R;
+      bulk_store(const_cast<uint32_t *>(u.cA) + (int64_t)j0 * W, smem_u32(&sm.band[buf][0][0]),
+                 (uint32_t)R * row_bytes);
+      int rb = (j0 + u.qy) % Cy;
+      if (rb < 0) rb += Cy;
+      const int n1 = min(R, Cy - rb);
+      const uint32_t src = smem_u32(&sm.band[buf][5][0]);
+      bulk_store(const_cast<uint32_t *>(u.cB) + (int64_t)rb * W, src, (uint32_t)n1 * row_bytes);
+      if (n1 < R)
+        bulk_store(const_cast<uint32_t *>(u.cB), src + (uint32_t)n1 * row_bytes,
+                   (uint32_t)(R - n1) * row_bytes);
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      // stage the tile after next into the buffer evaluated one tile ago, once
+      // its write-back (committed one tile ago) has read it
+      const int next2 = tile + 2 * gridDim.x;
+      if (next2 < ntiles) {
+        const int nb = buf == 0 ? kTileBufs - 1 : buf - 1;
+        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        stage(next2, nb);
+        staged |= 1u << nb;
+      }
+    }
+    buf = buf == kTileBufs - 1 ? 0 : buf + 1;
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (sm.err) {
+      // give copies still in flight a bounded chance to land before exiting
+      for (int b = 0; b < kTileBufs; ++b)
+        if (staged & (1u << b)) mbar_wait(smem_u32(&sm.mbar[b]), (par >> b) & 1u);
+      g.ctl[kCtlStatus] = 1;
+    }
+  }
+}
+
+// Lock-step phase of several lattices in one launch: each CTA works on one
+// lattice (its share of the grid is proportional to the lattice's words), with
+// that lattice's tables, phase counter and schedule.
+template <bool kAligned>
+__global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__restrict__ jobs,
+                                                             int njobs, int64_t p_off) {
+  __shared__ PhaseSmem sm;
+  __shared__ int s_job;
+  if (threadIdx.x == 0) {
+    int j = 0;
+    while (j + 1 < njobs && (int)blockIdx.x >= jobs[j + 1].cta_begin) ++j;
+    s_job = j;
+  }
+  __syncthreads();
+  const MultiJob &J = jobs[s_job];
+  const Geo g = J.g;
+  for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) sm.thrhi[t] = J.thrhi[t];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+  const uint64_t P = (uint64_t)(g.ctl[kCtlPhaseBase] + p_off);
+  if (threadIdx.x < 32) {
+    const Sched sc = draw_schedule(g, P);
+    if (threadIdx.x == 0) sm.sched = sc;
+  }
+  __syncthreads();
+  const Sched sc = sm.sched;
+  const uint32_t *trans = sc.near ? J.trans_near : J.trans_far;
+  for (int t = threadIdx.x; t < kTransN; t += blockDim.x)
+    sm.trans[t] = make_uint2(trans[2 * t], trans[2 * t + 1]);
+  __syncthreads();
+  const PhaseU u = phase_uniform(g, sc);
+  const int nw = g.Cy * g.W;
+  int wid = ((int)blockIdx.x - J.cta_begin) * blockDim.x + threadIdx.x;
+  const int stride = J.cta_count * blockDim.x;
+  int j = wid / g.W, w = wid - j * g.W;
+  const int sj = stride / g.W, sw = stride - sj * g.W;
+  for (; wid < nw; wid += stride) {
+    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, J.thr32, j, j, w,
+                                                      P);
+    w += sw;
+    j += sj;
+    if (w >= g.W) {
+      w -= g.W;
+      ++j;
+    }
+  }
+}
+
+// ============================================================================
+// Resident batch kernel (many lattices of uneven size, one persistent launch).
+// Each CTA takes lattices from a work queue, largest first; it holds the whole
+// packed lattice and its tables in shared memory and runs all of that lattice's
+// sweeps with block barriers between phases, recounting into the lattice's ring
+// when due; then it writes the lattice back and takes the next one.  The same
+// per-word code as phase_kernel runs against shared memory, so results are
+// identical to the per-phase launches.
+__global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict__ jobs, int njobs,
+                                                       int *queue) {
+  extern __shared__ __align__(16) uint32_t dyn[];
+  uint32_t *s_thrhi = dyn;
+  uint2 *s_far = reinterpret_cast<uint2 *>(dyn + kThrHiWords);
+  uint2 *s_near = s_far + kTransN;
+  uint32_t *s_words = dyn + kResTableWords;
+  __shared__ Sched s_sched;
+  __shared__ int s_job;
+  __shared__ int64_t s_red[32][7];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = atomicAdd(queue, 1);
+    __syncthreads();
+    const int job = s_job;
+    if (job >= njobs) break;
+    const JobDesc &J = jobs[job];
+    const Geo g = J.g;
+    const int64_t nw = 16 * g.cstride;
+    for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) s_thrhi[t] = J.thrhi[t];
+    for (int t = threadIdx.x; t < kTransN; t += blockDim.x) {
+      s_far[t] = make_uint2(J.trans_far[2 * t], J.trans_far[2 * t + 1]);
+      s_near[t] = make_uint2(J.trans_near[2 * t], J.trans_near[2 * t + 1]);
+    }
+    for (int64_t t = threadIdx.x; t < nw; t += blockDim.x) s_words[t] = g.words[t];
+    const int64_t P0 = g.ctl[kCtlPhaseBase];
+    const int64_t nsweeps = J.nsweeps;
+    const int obs_every = J.obs_every;
+    Geo gs = g;
+    gs.words = s_words;
+    const bool aligned = (g.Cx & 15) == 0;
+    const int nwa = g.Cy * g.W;  // a-words per phase
+    __syncthreads();
+    for (int64_t s = 0; s < nsweeps; ++s) {
+      for (int p = 0; p < 8; ++p) {
+        const uint64_t P = (uint64_t)(P0 + 8 * s + p);
+        if (threadIdx.x < 32) {
+          const Sched sc = draw_schedule(gs, P);
+          if (threadIdx.x == 0) s_sched = sc;
+        }
+        __syncthreads();
+        const Sched sc = s_sched;
+        const PhaseU u = phase_uniform(gs, sc);
+        const uint2 *tr = sc.near ? s_near : s_far;
+        for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
+          const int j = wid / g.W, w = wid - j * g.W;
+          if (aligned)
+            phase_word<kRowAligned>(gs, u, tr, s_thrhi, J.thr32, j, j, w, P);
+          else
+            phase_word<kRowGeneral>(gs, u, tr, s_thrhi, J.thr32, j, j, w, P);
+        }
+        __syncthreads();
+      }
+      const int64_t done = P0 / 8 + s + 1;
+      if (obs_every > 0 && done % obs_every == 0) {
+        int c[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int cls = 0; cls < 16; ++cls) count_class(gs, cls, threadIdx.x, blockDim.x, c);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+          const int64_t v = warp_sum((int64_t)c[k]);
+          if (lane == 0) s_red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          int64_t rec[8];
+          rec[0] = done;
+          for (int k = 0; k < 7; ++k) {
+            int64_t v = 0;
+            for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) v += s_red[wv][k];
+            rec[1 + k] = v;
+          }
+          for (int k = 0; k < 8; ++k) g.ctl[kCtlLatest + k] = rec[k];
+          const int64_t cnt = g.ctl[kCtlObsCount];
+          int64_t *dst = J.ring + (cnt % J.ring_cap) * 8;
+          for (int k = 0; k < 8; ++k) dst[k] = rec[k];
+          g.ctl[kCtlObsCount] = cnt + 1;
+          if (J.hist) {
+            const int64_t N = (int64_t)g.Lx * g.Ly;
+            const int64_t vals[3] = {rec[4], rec[5], rec[7]};
+            for (int h = 0; h < 3; ++h) J.hist[h * J.nbins + (vals[h] + N) * J.nbins / (2 * N + 1)] += 1;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int64_t t = threadIdx.x; t < nw; t += blockDim.x) g.words[t] = s_words[t];
+    if (threadIdx.x == 0) g.ctl[kCtlPhaseBase] = P0 + 8 * nsweeps;
+    __syncthreads();
+  }
+}
+
+int64_t resident_smem_bytes(int64_t max_words) {
+  return (int64_t)sizeof(uint32_t) * (kResTableWords + max_words);
+}
+
+cudaError_t launch_resident(const JobDesc *d_jobs, int njobs, int *d_queue, int grid, int threads,
+                            int64_t max_words, cudaStream_t s) {
+  const int64_t smem = resident_smem_bytes(max_words);
+  cudaError_t e = cudaFuncSetAttribute(resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  resident_kernel<<<grid, threads, (size_t)smem, s>>>(d_jobs, njobs, d_queue);
+  return cudaGetLastError();
+}
+
+// ============================================================================
+// Launchers.
+int phase_resident_grid(bool aligned) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const cudaError_t e =
+      aligned ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_kernel<true>, 256, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_kernel<false>, 256, 0);
+  if (e != cudaSuccess || per_sm < 1 || sms < 1) return 152 * 3;
+  return per_sm * sms;
+}
+
+bool tile_path_ok(const Geo &g) {
+  return (g.Cx & 15) == 0 && (g.W & 3) == 0 && g.W <= kTileWords && kTileWords % g.W == 0 &&
+         g.Cy % (kTileWords / g.W) == 0;
+}
+
+// Also raises the tile kernel's dynamic shared memory limit on the current
+// device (outside any stream capture: called when a lattice is created).  0
+// when that fails: the lattice then takes the direct path.
+int tile_resident_grid() {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaFuncSetAttribute(phase_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(TileSmem)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel, 256,
+                                                    sizeof(TileSmem)) != cudaSuccess ||
+      per_sm < 1 || sms < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * sms;
+}
+
+cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const LaunchCfg &cfg,
+                         cudaStream_t s) {
+  const int64_t nw = (int64_t)g.Cy * g.W;
+  if (cfg.tile_grid > 0) {
+    const int64_t tiles = nw / kTileWords;
+    const int grid = (int)(tiles < cfg.tile_grid ? tiles : cfg.tile_grid);
+    return launch_pdl_smem(phase_tile_kernel, grid, 256, sizeof(TileSmem), s, g, t.thrhi,
+                           t.thr32, t.trans_far, t.trans_near, p_off);
+  }
+  const int grid = grid_for(nw, 256, cfg.phase_grid_cap);
+  const uint32_t *thrhi = t.thrhi, *thr32 = t.thr32, *tf = t.trans_far, *tn = t.trans_near;
+  if ((g.Cx & 15) == 0)
+    return launch_pdl(phase_kernel<true>, grid, 256, s, g, thrhi, thr32, tf, tn, p_off);
+  return launch_pdl(phase_kernel<false>, grid, 256, s, g, thrhi, thr32, tf, tn, p_off);
+}
+
+cudaError_t launch_phase_multi(const MultiJob *d_jobs, int njobs, int grid, bool aligned,
+                               int64_t p_off, cudaStream_t s) {
+  if (aligned) return launch_pdl(phase_multi_kernel<true>, grid, 256, s, d_jobs, njobs, p_off);
+  return launch_pdl(phase_multi_kernel<false>, grid, 256, s, d_jobs, njobs, p_off);
+}
+
+}  // namespace ccmc
