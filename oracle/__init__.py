@@ -59,6 +59,9 @@ def lib():
             "oracle_sequential_sweeps": (c_int64, [u8p, c_int, c_int, c_uint64, c_int64, c_int64,
                                                    c_double, c_double, c_double, c_double, c_int,
                                                    i64p]),
+            "oracle_neighbour_sweeps": (c_int64, [u8p, c_int, c_int, c_uint64, c_int64, c_int64,
+                                                  c_double, c_double, c_double, c_double, c_int,
+                                                  i64p]),
             "oracle_enumerate": (c_int64, [c_int, c_int, c_int, i64p, i64p, i64p, i64p]),
         }
         for name, (res, args) in sig.items():
@@ -167,12 +170,20 @@ def phase(st: np.ndarray, seed: int, P: int, table) -> None:
 
 
 def sweeps(st: np.ndarray, seed: int, sweep0: int, nsweeps: int, beta: float, Delta: float,
-           V: float, J: float, obs_every: int = 0, sequential: bool = False) -> np.ndarray:
-    """Advance ``st`` in place; returns the int64 records (rows of REC_FIELDS)."""
+           V: float, J: float, obs_every: int = 0, sequential: bool = False,
+           neighbour: bool = False) -> np.ndarray:
+    """Advance ``st`` in place; returns the int64 records (rows of REC_FIELDS).
+
+    Default: the colour-phase chain.  ``sequential``: one uniformly random
+    ordered pair per move.  ``neighbour``: the short-range negative control
+    (partner among a's four nearest neighbours)."""
     Ly, Lx = st.shape
     nrec_max = nsweeps // obs_every + 1 if obs_every > 0 else 0
     rec = np.zeros((max(nrec_max, 1), REC), dtype=np.int64)
-    fn = lib().oracle_sequential_sweeps if sequential else lib().oracle_sweeps
+    if neighbour:
+        fn = lib().oracle_neighbour_sweeps
+    else:
+        fn = lib().oracle_sequential_sweeps if sequential else lib().oracle_sweeps
     n = fn(_u8(st), Lx, Ly, seed & ((1 << 64) - 1), sweep0, nsweeps, beta, Delta, V, J,
            obs_every, _p(rec, c_int64))
     if n < 0:

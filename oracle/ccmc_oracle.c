@@ -448,3 +448,57 @@ int64_t oracle_sequential_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int
   free(table);
   return nrec;
 }
+
+/* Short-range pair mode: the paper's first version, abandoned because it
+ * misses low-temperature results on 4 x 4 (Sec. 3.2).  Each move picks site a
+ * uniformly and its partner b uniformly among a's four nearest neighbours
+ * (right, left, down, up), then makes the coupled-pair move of Sec. 3.1; N/2
+ * moves per sweep.  Random words: Philox(seed, (t_lo, t_hi, attempt, NN)) with
+ * t the global move index; words 0-1 give (a, direction) by Lemire's
+ * multiply-high over 4N with rejection, word 2 is the pair's move word. */
+int64_t oracle_neighbour_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
+                                int64_t nsweeps, double beta, double Delta, double V, double J,
+                                int obs_every, int64_t *records) {
+  uint32_t key[2];
+  seed_key(seed, key);
+  uint32_t *table = (uint32_t *)malloc(sizeof(uint32_t) * ORACLE_TABLE_SIZE);
+  if (!table) return -1;
+  oracle_threshold_table(beta, Delta, V, J, table);
+  uint64_t N = (uint64_t)Lx * (uint64_t)Ly;
+  uint64_t nchoices = 4 * N;
+  uint64_t reject_below = (0 - nchoices) % nchoices;
+  int64_t moves = (int64_t)(N / 2);
+  int64_t nrec = 0;
+  for (int64_t s = 0; s < nsweeps; ++s) {
+    int64_t sweep = sweep0 + s;
+    for (int64_t mv = 0; mv < moves; ++mv) {
+      uint64_t t = (uint64_t)(sweep * moves + mv);
+      for (uint32_t attempt = 0; attempt < 64; ++attempt) {
+        uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), attempt, ORACLE_TAG_NN};
+        uint32_t w[4];
+        oracle_philox4x32_10(ctr, key, w);
+        uint64_t x = ((uint64_t)w[1] << 32) | (uint64_t)w[0];
+        unsigned __int128 m = (unsigned __int128)x * (unsigned __int128)nchoices;
+        if ((uint64_t)m < reject_below) continue;
+        uint64_t pidx = (uint64_t)(m >> 64);
+        int a = (int)(pidx / 4), dir = (int)(pidx % 4);
+        int ax = a % Lx, ay = a / Lx;
+        int bx = ax, by = ay;
+        if (dir == 0) bx = (ax + 1) % Lx;
+        else if (dir == 1) bx = (ax + Lx - 1) % Lx;
+        else if (dir == 2) by = (ay + 1) % Ly;
+        else by = (ay + Ly - 1) % Ly;
+        int b = by * Lx + bx;
+        uint32_t sctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), attempt, ORACLE_TAG_NNSLOW};
+        oracle_pair_move(st, Lx, Ly, a, b, w[2], key, sctr, table);
+        break;
+      }
+    }
+    if (obs_every > 0 && (sweep + 1) % obs_every == 0 && records) {
+      write_record(st, Lx, Ly, sweep + 1, records + ORACLE_REC * nrec);
+      ++nrec;
+    }
+  }
+  free(table);
+  return nrec;
+}

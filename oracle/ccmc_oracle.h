@@ -36,6 +36,8 @@ extern "C" {
 #define ORACLE_TAG_SIGN 5u    /* initial spin signs of magnetic sites       */
 #define ORACLE_TAG_SEQ 6u     /* sequential random-pair mode: pair + u_hi   */
 #define ORACLE_TAG_SEQSLOW 7u /* sequential random-pair mode: slow words    */
+#define ORACLE_TAG_NN 8u      /* short-range pair mode: pair + u_hi        */
+#define ORACLE_TAG_NNSLOW 9u  /* short-range pair mode: slow words         */
 
 /* Threshold table: dQ in [-2,2], dBV and dBJ in [-ORACLE_DB, ORACLE_DB]. */
 #define ORACLE_DB 24
@@ -100,6 +102,12 @@ int64_t oracle_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0
 int64_t oracle_sequential_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
                                  int64_t nsweeps, double beta, double Delta, double V, double J,
                                  int obs_every, int64_t *records);
+/* Short-range pair mode (Sec. 3.2's abandoned first version): partner b is a
+ * uniformly chosen nearest neighbour of a uniformly chosen a; N/2 moves per
+ * sweep.  A negative control for tests, not a method of the library. */
+int64_t oracle_neighbour_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
+                                int64_t nsweeps, double beta, double Delta, double V, double J,
+                                int obs_every, int64_t *records);
 
 /* Exact enumeration of the states with sum S = Q (N <= 16): histogram over
  * (Nc, BV, BJ) with bins [Nc][BV + 2N][BJ + 2N] of size (N+1) x (4N+1) x (4N+1);

@@ -9,7 +9,10 @@ Eq. (2).  Checked against:
 * Delta -> +inf: charge creation is never accepted, so Nc falls to |Q| and
   stays; Delta -> -inf: every site ends up charged, Nc = N, BJ = 0;
 * the Ising limit: transfer matrix on 4 x 4 and 8 x 8;
-* colour schedule vs sequential random pairs on 8 x 8.
+* colour schedule vs sequential random pairs on 8 x 8;
+* a negative control: nearest-neighbour partners only (the paper's abandoned
+  first version, Sec. 3.2) miss the low-temperature heat-capacity peak of
+  4 x 4 that the colour schedule reproduces.
 
 Means are compared within 4 standard errors from batch means.
 """
@@ -189,3 +192,49 @@ def test_transfer_matrix_matches_brute_force(L):
     e_tm, c_tm = ising_energy_and_heat(L, T, J)
     assert abs(e_tm - e1 / N) < 1e-10
     assert abs(c_tm - (e2 - e1 * e1) / (N * T * T)) < 1e-9
+
+
+def test_short_range_pairs_miss_the_low_temperature_peak():
+    """Negative control (Sec. 3.2): the paper's first version took the partner
+    among a's nearest neighbours and, on 4 x 4, lost the heat capacity's
+    low-temperature peak.  With Q = 2, Delta = -0.5, V = J = 1 the exact C(T)
+    of 4 x 4 has a low-temperature peak at T = 0.25 besides the main one; the
+    colour-schedule chain reproduces it, the short-range chain freezes in a
+    metastable state (some states are out of its reach at that temperature)
+    and misses it."""
+    Q, Delta, V, J = 2, -0.5, 1.0, 1.0
+    # the exact curve: a local maximum at T = 0.25, well below the main peak
+    C = {T: exact_averages(4, 4, Q, T, Delta, V, J)["C"] for T in (0.15, 0.25, 0.4, 1.6)}
+    assert C[0.25] > 1.5 * C[0.15] and C[0.25] > 1.5 * C[0.4]
+    assert C[1.6] > 5 * C[0.25]
+    T = 0.25
+    ex = exact_averages(4, 4, Q, T, Delta, V, J)
+    n_plus = max(Q, 0) + 14 // 4
+    st = oracle.init_counts(4, 4, 5, n_plus, n_plus - Q)
+    rec = oracle.sweeps(st, 5, 0, 200000, 1.0 / T, Delta, V, J, obs_every=1)[2000:]
+    E = energy(rec, Delta, V, J)
+    c_all, s_all = batch_heat(E, 16, T)
+    e_all, se_all = batch_mean(E / 16)
+    assert abs(c_all - ex["C"]) <= 4 * s_all
+    assert abs(e_all - ex["E"]) <= 4 * max(se_all, 1e-12)
+    st = oracle.init_counts(4, 4, 5, n_plus, n_plus - Q)
+    rec = oracle.sweeps(st, 5, 0, 200000, 1.0 / T, Delta, V, J, obs_every=1,
+                        neighbour=True)[2000:]
+    assert np.all(rec[:, 6] == Q)
+    E = energy(rec, Delta, V, J)
+    c_nn, _ = batch_heat(E, 16, T)
+    e_nn, _ = batch_mean(E / 16)
+    assert c_nn < 0.25 * ex["C"]                       # the peak is missing
+    assert e_nn - ex["E"] > 0.02 and e_nn - ex["E"] > 20 * se_all  # stuck above
+
+
+def test_short_range_pairs_agree_at_high_temperature():
+    """The short-range chain is a valid Metropolis chain (symmetric proposals,
+    charge conserved): away from the low-temperature region it reproduces the
+    exact averages, so the failure above is specific to low temperature."""
+    Q, Delta, V, J, T = 2, -0.5, 1.0, 1.0, 1.6
+    n_plus = max(Q, 0) + 14 // 4
+    st = oracle.init_counts(4, 4, 9, n_plus, n_plus - Q)
+    rec = oracle.sweeps(st, 9, 0, 200000, 1.0 / T, Delta, V, J, obs_every=1,
+                        neighbour=True)[2000:]
+    compare(rec, exact_averages(4, 4, Q, T, Delta, V, J), 16, T, Delta, V, J)
