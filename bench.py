@@ -284,6 +284,62 @@ def measure_batched(cc, nsweeps=5000, plain_sample=32, plain_sweeps=200):
             "speedup_vs_plain": (work / dt) / plain}
 
 
+def measure_paper_maps(cc, L=4096, nmaps=40, batch=8):
+    """The paper's own parallel scheme (Sec. 3.2) on one lattice of the
+    workload: maps of N/10 pairs built on the host by random marking (all host
+    cores), copied to the GPU and applied one kernel per map.  Reports the host
+    generation rate, the device rate with maps already built, the pipelined
+    rate (the host builds the next batch while the GPU applies the current
+    one) and the colour schedule's rate on the same lattice."""
+    import torch
+
+    from workloads import temperature_sweep_4096
+
+    s = temperature_sweep_4096()[1]
+    P = cc.map_size(L, L)
+    updates_per_map = 2 * P
+    stream = torch.cuda.Stream()
+    with cc.Lattice(L, L, stream=stream) as lat:
+        lat.init_constrained(s.seed, s.n, s.charged_frac)
+        t0 = time.perf_counter()
+        maps = cc.maps_build(L, L, s.seed, 0, nmaps)
+        t_gen = time.perf_counter() - t0
+        lat.map_apply(maps[:2], 0, s.beta, s.Delta, s.V, s.J)  # warm-up
+        lat.sync()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.map_apply(maps, 0, s.beta, s.Delta, s.V, s.J)
+        b.record(stream)
+        lat.sync()
+        t_dev = a.elapsed_time(b) / 1e3  # copy of all maps + one kernel per map
+        t0 = time.perf_counter()
+        for k in range(0, nmaps, batch):
+            m = cc.maps_build(L, L, s.seed, nmaps + k, batch)
+            lat.map_apply(m, nmaps + k, s.beta, s.Delta, s.V, s.J)
+        lat.sync()
+        t_pipe = time.perf_counter() - t0
+        lat.sweep(2, s.beta, s.Delta, s.V, s.J)
+        lat.sync()
+        a.record(stream)
+        lat.sweep(16, s.beta, s.Delta, s.V, s.J)
+        b.record(stream)
+        lat.sync()
+        t_col = a.elapsed_time(b) / 1e3
+    return {
+        "workload": f"{L}x{L} at T={s.T} (Delta={s.Delta}, V={s.V}, J={s.J}): {nmaps} maps of "
+                    f"{P} pairs (N/10)",
+        "host_threads": os.cpu_count(),
+        "host_generation": {"value": nmaps * updates_per_map / t_gen, "unit": "site-updates/s",
+                            "ms_per_map": 1e3 * t_gen / nmaps},
+        "device_only": {"value": nmaps * updates_per_map / t_dev, "unit": "site-updates/s",
+                        "ms_per_map": 1e3 * t_dev / nmaps,
+                        "h2d_bytes_per_map": 8 * P},
+        "pipelined": {"value": nmaps * updates_per_map / t_pipe, "unit": "site-updates/s"},
+        "colour_schedule": {"value": 16 * L * L / t_col, "unit": "site-updates/s"},
+    }
+
+
 def measure_served(cc, count=120, plain_sample=24):
     """Poisson request stream (200 req/s; L log-uniform in [32, 2048]; sweeps
     log-uniform in [1e3, 1e5]) through the continuous-batching server under a
@@ -479,6 +535,7 @@ def run_ours(args):
         if not args.no_side and args.workload == "temperature4096":
             line["batched"] = measure_batched(cc)
             line["served"] = measure_served(cc)
+            line["paper_maps"] = measure_paper_maps(cc)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample(sims)
         print(json.dumps(line), flush=True)

@@ -235,6 +235,50 @@ int ccmc_threshold_table(double beta, double Delta, double V, double J, uint32_t
 int ccmc_philox_device(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                        uint32_t k1, int64_t count, uint32_t *out);
 
+/* ---- Paper-faithful map mode (Sec. 3.2, the algorithm for building a map) --
+ * The paper's own parallel scheme: maps of non-interacting pairs built on the
+ * host by random marking, copied to the GPU and processed one after another,
+ * each pair of a map by its own thread.  ccmc_sweep's colour phases replace it
+ * in this library; the mode is kept to compare both (statistics, and the cost
+ * of host generation plus transfer).
+ *
+ * A map of an Lx x Ly lattice holds P = max(1, floor(Lx Ly / 10)) pairs.  It is
+ * built with an array of N flags, all clear: draw a site until it is unmarked
+ * and mark it (a), the same for b (b may be a neighbour of a), append (a, b),
+ * mark the four nearest neighbours of a and of b, and repeat until P pairs are
+ * listed.  Draw d of map m uses words 2 (d mod 2) and 2 (d mod 2) + 1 of
+ * Philox4x32-10(seed; d / 2, m_lo, m_hi, 10) as a 64-bit x: the site is the
+ * high half of x * N, redrawn when the low half is below 2^64 mod N. */
+
+/* Pairs per map, max(1, floor(Lx Ly / 10)); E_INVAL if Lx or Ly < 2. */
+int64_t ccmc_map_size(int Lx, int Ly);
+
+/* Host-only (no GPU needed): builds maps map0 .. map0 + nmaps - 1 for the
+ * given seed into pairs_out, caller-owned, 2 * P * nmaps int32: for each pair
+ * the site indices y * Lx + x of a, then b; map k starts at pairs_out + 2 P k.
+ * nthreads host threads build maps in parallel (<= 0: one per core); the
+ * result does not depend on it.  Lx, Ly >= 2, Lx * Ly <= 2^31.
+ * Errors: E_INVAL, E_NOMEM. */
+int ccmc_maps_build(int Lx, int Ly, uint64_t seed, int64_t map0, int64_t nmaps,
+                    int32_t *pairs_out, int nthreads);
+
+/* Applies maps map0 .. map0 + nmaps - 1 (host memory, laid out as
+ * ccmc_maps_build writes them for this lattice's shape) to the lattice at
+ * (beta, Delta, V, J): the pairs are copied into device memory the lattice
+ * owns and one kernel per map makes the coupled-pair move of Sec. 3.1 for
+ * every pair of the map.  Pair p of map m draws its move word from
+ * Philox4x32-10(seed; p, m_lo, m_hi, 11) and, when the choice field is >= 65532
+ * or the acceptance needs the low half, its slow words from (p, m_lo, m_hi,
+ * 12), with the choice and acceptance rules of ccmc_sweep; the seed is the
+ * lattice's.  Every index must lie in [0, Lx Ly) (checked: E_INVAL); maps that
+ * do not come from ccmc_maps_build may break the sampling but not memory
+ * safety.  The work is queued on the lattice's stream; the call returns once
+ * `pairs` has been copied.  The colour-phase position is unchanged; read the
+ * result with ccmc_observables or ccmc_get_state.
+ * Errors: E_INVAL, E_STATE (not initialised), E_NOMEM, E_CUDA. */
+int ccmc_map_apply(ccmc_lattice *h, const int32_t *pairs, int64_t map0, int64_t nmaps,
+                   double beta, double Delta, double V, double J);
+
 const char *ccmc_strerror(int code);
 
 #ifdef __cplusplus

@@ -17,7 +17,7 @@ Lattices are ``uint8`` arrays of shape (Ly, Lx), codes 0: s=+1/2, 1: s=-1/2,
 from __future__ import annotations
 
 import ctypes
-from ctypes import POINTER, c_double, c_int, c_int64, c_uint32, c_uint64
+from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_uint32, c_uint64
 
 import numpy as np
 
@@ -39,7 +39,7 @@ def lib():
         path = _build.build()
         L = ctypes.CDLL(path)
         u32p, u8p, i64p = POINTER(c_uint32), POINTER(ctypes.c_uint8), POINTER(c_int64)
-        ip = POINTER(c_int)
+        ip, i32p = POINTER(c_int), POINTER(c_int32)
         sig = {
             "oracle_philox4x32_10": (None, [u32p, u32p, u32p]),
             "oracle_charge_counts": (c_int, [c_int64, c_double, c_double, i64p, i64p, i64p]),
@@ -62,6 +62,10 @@ def lib():
             "oracle_neighbour_sweeps": (c_int64, [u8p, c_int, c_int, c_uint64, c_int64, c_int64,
                                                   c_double, c_double, c_double, c_double, c_int,
                                                   i64p]),
+            "oracle_map_size": (c_int64, [c_int, c_int]),
+            "oracle_map_build": (c_int, [c_int, c_int, c_uint64, c_int64, i32p]),
+            "oracle_map_sweeps": (c_int64, [u8p, c_int, c_int, c_uint64, c_int64, c_int64,
+                                            c_double, c_double, c_double, c_double, c_int, i64p]),
             "oracle_enumerate": (c_int64, [c_int, c_int, c_int, i64p, i64p, i64p, i64p]),
         }
         for name, (res, args) in sig.items():
@@ -186,6 +190,34 @@ def sweeps(st: np.ndarray, seed: int, sweep0: int, nsweeps: int, beta: float, De
         fn = lib().oracle_sequential_sweeps if sequential else lib().oracle_sweeps
     n = fn(_u8(st), Lx, Ly, seed & ((1 << 64) - 1), sweep0, nsweeps, beta, Delta, V, J,
            obs_every, _p(rec, c_int64))
+    if n < 0:
+        raise MemoryError("oracle allocation failed")
+    return rec[:n]
+
+
+def map_size(Lx: int, Ly: int) -> int:
+    """Pairs per paper map: max(1, floor(N / 10))."""
+    return int(lib().oracle_map_size(Lx, Ly))
+
+
+def map_build(Lx: int, Ly: int, seed: int, m: int) -> np.ndarray:
+    """Map m of the paper's random-marking algorithm: (P, 2) site indices."""
+    P = map_size(Lx, Ly)
+    out = np.zeros((P, 2), dtype=np.int32)
+    if lib().oracle_map_build(Lx, Ly, seed & ((1 << 64) - 1), m, _p(out, c_int32)) != 0:
+        raise MemoryError("oracle allocation failed")
+    return out
+
+
+def map_sweeps(st: np.ndarray, seed: int, map0: int, nmaps: int, beta: float, Delta: float,
+               V: float, J: float, obs_every: int = 0) -> np.ndarray:
+    """Apply paper maps map0 .. map0 + nmaps - 1 to ``st`` in place; records
+    after every obs_every-th map (sweeps_done = maps done)."""
+    Ly, Lx = st.shape
+    nrec_max = nmaps // obs_every + 1 if obs_every > 0 else 0
+    rec = np.zeros((max(nrec_max, 1), REC), dtype=np.int64)
+    n = lib().oracle_map_sweeps(_u8(st), Lx, Ly, seed & ((1 << 64) - 1), map0, nmaps, beta,
+                                Delta, V, J, obs_every, _p(rec, c_int64))
     if n < 0:
         raise MemoryError("oracle allocation failed")
     return rec[:n]

@@ -502,3 +502,106 @@ int64_t oracle_neighbour_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int6
   free(table);
   return nrec;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Paper-faithful maps (Sec. 3.2, the algorithm for building a map).  A map is
+ * a list of P = max(1, floor(N / 10)) pairs built by random marking on an
+ * L x L array of flags, all clear at first: draw a site until it is unmarked,
+ * mark it (site a); draw and mark site b the same way (b may be a neighbour
+ * of a); add (a, b); mark the nearest neighbours of a and of b; repeat until
+ * the map holds P pairs.  Later pairs never touch an earlier pair's sites or
+ * their neighbours, so the pairs of a map do not interact.
+ *
+ * Draws of map m: draw d uses words 2(d mod 2), 2(d mod 2) + 1 of
+ * Philox(seed, (d / 2, m_lo, m_hi, MAP)) as a 64-bit x; the site is the high
+ * word of x * N unless the low word is below 2^64 mod N (rejected: next d).
+ * Moves: pair p of map m takes word 0 of Philox(seed, (p, m_lo, m_hi,
+ * MAPMOVE)) as its move word and (p, m_lo, m_hi, MAPSLOW) as its slow
+ * counter (oracle_pair_move). */
+int64_t oracle_map_size(int Lx, int Ly) {
+  int64_t P = (int64_t)Lx * Ly / 10;
+  return P < 1 ? 1 : P;
+}
+
+int oracle_map_build(int Lx, int Ly, uint64_t seed, int64_t m, int32_t *pairs) {
+  uint32_t key[2];
+  seed_key(seed, key);
+  uint64_t N = (uint64_t)Lx * (uint64_t)Ly;
+  int64_t P = oracle_map_size(Lx, Ly);
+  uint8_t *marked = (uint8_t *)calloc((size_t)N, 1);
+  if (!marked) return -1;
+  uint64_t reject_below = (0 - N) % N;
+  uint64_t d = 0;
+  uint32_t w[4];
+  for (int64_t p = 0; p < P; ++p) {
+    int site[2];
+    for (int k = 0; k < 2; ++k) {
+      for (;;) {
+        if ((d & 1) == 0) {
+          uint32_t ctr[4] = {(uint32_t)(d >> 1), (uint32_t)m, (uint32_t)((uint64_t)m >> 32),
+                             ORACLE_TAG_MAP};
+          oracle_philox4x32_10(ctr, key, w);
+        }
+        int h = (int)(d & 1);
+        ++d;
+        uint64_t x = ((uint64_t)w[2 * h + 1] << 32) | (uint64_t)w[2 * h];
+        unsigned __int128 prod = (unsigned __int128)x * (unsigned __int128)N;
+        if ((uint64_t)prod < reject_below) continue;
+        int cand = (int)(uint64_t)(prod >> 64);
+        if (marked[cand]) continue;
+        marked[cand] = 1;
+        site[k] = cand;
+        break;
+      }
+    }
+    pairs[2 * p] = site[0];
+    pairs[2 * p + 1] = site[1];
+    for (int k = 0; k < 2; ++k) {
+      int nb[4];
+      neighbours(Lx, Ly, site[k], nb);
+      for (int t = 0; t < 4; ++t) marked[nb[t]] = 1;
+    }
+  }
+  free(marked);
+  return 0;
+}
+
+int64_t oracle_map_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t map0, int64_t nmaps,
+                          double beta, double Delta, double V, double J, int obs_every,
+                          int64_t *records) {
+  uint32_t key[2];
+  seed_key(seed, key);
+  int64_t P = oracle_map_size(Lx, Ly);
+  uint32_t *table = (uint32_t *)malloc(sizeof(uint32_t) * ORACLE_TABLE_SIZE);
+  int32_t *pairs = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)P);
+  if (!table || !pairs) {
+    free(table);
+    free(pairs);
+    return -1;
+  }
+  oracle_threshold_table(beta, Delta, V, J, table);
+  int64_t nrec = 0;
+  for (int64_t k = 0; k < nmaps; ++k) {
+    int64_t m = map0 + k;
+    if (oracle_map_build(Lx, Ly, seed, m, pairs) != 0) {
+      nrec = -1;
+      break;
+    }
+    for (int64_t p = 0; p < P; ++p) {
+      uint32_t ctr[4] = {(uint32_t)p, (uint32_t)m, (uint32_t)((uint64_t)m >> 32),
+                         ORACLE_TAG_MAPMOVE};
+      uint32_t w[4];
+      oracle_philox4x32_10(ctr, key, w);
+      uint32_t sctr[4] = {(uint32_t)p, (uint32_t)m, (uint32_t)((uint64_t)m >> 32),
+                          ORACLE_TAG_MAPSLOW};
+      oracle_pair_move(st, Lx, Ly, pairs[2 * p], pairs[2 * p + 1], w[0], key, sctr, table);
+    }
+    if (obs_every > 0 && (m + 1) % obs_every == 0 && records) {
+      write_record(st, Lx, Ly, m + 1, records + ORACLE_REC * nrec);
+      ++nrec;
+    }
+  }
+  free(pairs);
+  free(table);
+  return nrec;
+}

@@ -38,6 +38,9 @@ extern "C" {
 #define ORACLE_TAG_SEQSLOW 7u /* sequential random-pair mode: slow words    */
 #define ORACLE_TAG_NN 8u      /* short-range pair mode: pair + u_hi        */
 #define ORACLE_TAG_NNSLOW 9u  /* short-range pair mode: slow words         */
+#define ORACLE_TAG_MAP 10u    /* paper maps: random-marking site draws      */
+#define ORACLE_TAG_MAPMOVE 11u /* paper maps: per pair, choice | u_hi       */
+#define ORACLE_TAG_MAPSLOW 12u /* paper maps: per pair, slow words          */
 
 /* Threshold table: dQ in [-2,2], dBV and dBJ in [-ORACLE_DB, ORACLE_DB]. */
 #define ORACLE_DB 24
@@ -108,6 +111,19 @@ int64_t oracle_sequential_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int
 int64_t oracle_neighbour_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
                                 int64_t nsweeps, double beta, double Delta, double V, double J,
                                 int obs_every, int64_t *records);
+
+/* Paper-faithful maps (Sec. 3.2): P = max(1, floor(N/10)) non-interacting
+ * pairs built by random marking; map m's pairs as site indices y*Lx + x,
+ * a then b, into pairs[2P].  Returns 0, or -1 if memory runs out. */
+int64_t oracle_map_size(int Lx, int Ly);
+int oracle_map_build(int Lx, int Ly, uint64_t seed, int64_t m, int32_t *pairs);
+
+/* Applies maps map0 .. map0 + nmaps - 1 in turn, each pair of a map once (in
+ * list order; the pairs do not interact).  Records after map m when
+ * (m + 1) % obs_every == 0, with sweeps_done = m + 1 (maps done). */
+int64_t oracle_map_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t map0, int64_t nmaps,
+                          double beta, double Delta, double V, double J, int obs_every,
+                          int64_t *records);
 
 /* Exact enumeration of the states with sum S = Q (N <= 16): histogram over
  * (Nc, BV, BJ) with bins [Nc][BV + 2N][BJ + 2N] of size (N+1) x (4N+1) x (4N+1);

@@ -101,6 +101,11 @@ def _load():
         "ccmc_server_release": (c_int, [vp, c_uint64]),
         "ccmc_server_stats_get": (c_int, [vp, POINTER(ServerStats)]),
         "ccmc_server_stop": (c_int, [vp]),
+        "ccmc_map_size": (c_int64, [c_int, c_int]),
+        "ccmc_maps_build": (c_int, [c_int, c_int, c_uint64, c_int64, c_int64,
+                                    POINTER(ctypes.c_int32), c_int]),
+        "ccmc_map_apply": (c_int, [vp, POINTER(ctypes.c_int32), c_int64, c_int64, c_double,
+                                   c_double, c_double, c_double]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -150,6 +155,29 @@ def philox_device(ctr, key, count: int) -> np.ndarray:
     return out.reshape(count, 4)
 
 
+def map_size(Lx: int, Ly: int) -> int:
+    """Pairs per paper map (Sec. 3.2): max(1, floor(Lx Ly / 10))."""
+    n = int(lib().ccmc_map_size(Lx, Ly))
+    if n < 0:
+        raise CcmcError(n, "ccmc_map_size")
+    return n
+
+
+def maps_build(Lx: int, Ly: int, seed: int, map0: int, nmaps: int, nthreads: int = 0,
+               out: np.ndarray = None) -> np.ndarray:
+    """Host-built paper maps map0 .. map0 + nmaps - 1: int32 array (nmaps, P, 2)
+    of site indices y * Lx + x (a, b) -- the random-marking algorithm of Sec. 3.2."""
+    P = map_size(Lx, Ly)
+    if out is None:
+        out = np.empty((nmaps, P, 2), dtype=np.int32)
+    if out.dtype != np.int32 or not out.flags.c_contiguous or out.size < 2 * P * nmaps:
+        raise ValueError("out must be a C-contiguous int32 array of nmaps * P * 2 entries")
+    _check(lib().ccmc_maps_build(Lx, Ly, seed & (2 ** 64 - 1), map0, nmaps,
+                                 out.ctypes.data_as(POINTER(ctypes.c_int32)), nthreads),
+           "ccmc_maps_build")
+    return out
+
+
 class Lattice:
     """An Lx x Ly lattice resident on the current CUDA device."""
 
@@ -193,6 +221,16 @@ class Lattice:
     def phases(self, nphases: int, beta: float, Delta: float, V: float, J: float):
         """Run nphases colour phases (the paper's "steps", one map each)."""
         _check(lib().ccmc_phases(self._h, nphases, beta, Delta, V, J), "ccmc_phases")
+
+    def map_apply(self, pairs: np.ndarray, map0: int, beta: float, Delta: float, V: float,
+                  J: float):
+        """Apply host-built paper maps (maps_build's layout, nmaps = len(pairs))
+        with one kernel per map; returns once the maps have been copied."""
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+        if pairs.ndim != 3 or pairs.shape[2] != 2:
+            raise ValueError("pairs must have shape (nmaps, P, 2)")
+        _check(lib().ccmc_map_apply(self._h, pairs.ctypes.data_as(POINTER(ctypes.c_int32)),
+                                    map0, pairs.shape[0], beta, Delta, V, J), "ccmc_map_apply")
 
     def sync(self):
         _check(lib().ccmc_sync(self._h), "ccmc_sync")

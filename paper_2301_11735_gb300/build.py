@@ -1,9 +1,11 @@
 """Build ``libccmc.so`` in-tree (``paper_2301_11735_gb300/_build``) for sm_103a.
 
-Six translation units are compiled in parallel and linked into one shared
+Eight translation units are compiled in parallel and linked into one shared
 library that exports the C ABI of ``include/ccmc.h``:
 
 * ``csrc/ccmc_phase.cu``   -- the colour-phase kernels (nvcc, sm_103a only);
+* ``csrc/ccmc_map.cu``     -- the paper-faithful map mode's kernel;
+* ``csrc/ccmc_maps.cpp``   -- host map generation (g++, host threads);
 * ``csrc/ccmc_kernels.cu`` -- the other CUDA kernels (init, recount, packing);
 * ``csrc/ccmc_api.cu``     -- host code of the C ABI (nvcc host pass);
 * ``csrc/ccmc_noalloc.cu`` -- the recount entry point that allocates nothing;
@@ -63,6 +65,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         common += ["-Xptxas", "-v"]
     jobs = {
         "ccmc_phase.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_phase.cu")],
+        "ccmc_map.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_map.cu")],
         "ccmc_kernels.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_kernels.cu")],
         "ccmc_api.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_api.cu")],
         "ccmc_noalloc.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_noalloc.cu")],
@@ -71,6 +74,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
                           os.path.join(CSRC, "ccmc_tables.cpp")],
         "ccmc_server.o": [os.environ.get("CXX", "g++"), "-c", "-std=c++17", "-O2", "-fPIC",
                           "-pthread", f"-I{cuda}/include", os.path.join(CSRC, "ccmc_server.cpp")],
+        "ccmc_maps.o": [os.environ.get("CXX", "g++"), "-c", "-std=c++17", "-O2", "-fPIC",
+                        "-pthread", os.path.join(CSRC, "ccmc_maps.cpp")],
     }
     procs = []
     for obj, cmd in jobs.items():

@@ -13,6 +13,7 @@
 
 #include "../../include/ccmc.h"
 #include "ccmc_internal.h"
+#include "ccmc_map.h"
 
 using namespace ccmc;
 
@@ -62,6 +63,9 @@ struct ccmc_lattice {
   double params[4] = {0, 0, 0, 0};  // beta, Delta, V, J
   LaunchCfg cfg{};
   std::vector<GraphEntry> graphs;
+  int32_t *d_maps = nullptr;  // paper-map mode: uploaded pairs
+  int64_t map_cap = 0;        // int32 entries held by d_maps
+  cudaEvent_t map_ev = nullptr;
 };
 
 namespace {
@@ -315,6 +319,8 @@ int ccmc_lattice_destroy(ccmc_lattice *h) {
   cudaFree(h->d_tables);
   cudaFree(h->d_bytes);
   cudaFree(h->d_flag);
+  cudaFree(h->d_maps);
+  if (h->map_ev) cudaEventDestroy(h->map_ev);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return CCMC_OK;
@@ -402,6 +408,44 @@ int ccmc_phases(ccmc_lattice *h, int64_t nphases, double beta, double Delta, dou
 int ccmc_sync(ccmc_lattice *h) {
   if (!h) return CCMC_E_INVAL;
   return check_status(h);
+}
+
+int ccmc_map_apply(ccmc_lattice *h, const int32_t *pairs, int64_t map0, int64_t nmaps,
+                   double beta, double Delta, double V, double J) {
+  if (!h || map0 < 0 || nmaps < 0 || (nmaps > 0 && !pairs) || !(beta >= 0.0) ||
+      !std::isfinite(Delta) || !std::isfinite(V) || !std::isfinite(J))
+    return CCMC_E_INVAL;
+  if (!h->initialised) return CCMC_E_STATE;
+  if (nmaps == 0) return CCMC_OK;
+  const int64_t P = ccmc_map_size(h->g.Lx, h->g.Ly);
+  const int64_t N = (int64_t)h->g.Lx * h->g.Ly;
+  if (nmaps > ((int64_t)1 << 40) / (2 * P)) return CCMC_E_INVAL;
+  const int64_t n = 2 * P * nmaps;
+  // the kernel addresses the lattice with these indices: reject any outside it
+  for (int64_t i = 0; i < n; ++i)
+    if (pairs[i] < 0 || pairs[i] >= N) return CCMC_E_INVAL;
+  if (!h->map_ev && cudaEventCreateWithFlags(&h->map_ev, cudaEventDisableTiming) != cudaSuccess)
+    return CCMC_E_CUDA;
+  if (n > h->map_cap) {
+    CK(cudaStreamSynchronize(h->stream));  // earlier maps may still be in use
+    cudaFree(h->d_maps);
+    h->d_maps = nullptr;
+    h->map_cap = 0;
+    if (cudaMalloc(&h->d_maps, sizeof(int32_t) * n) != cudaSuccess) {
+      cudaGetLastError();
+      return CCMC_E_NOMEM;
+    }
+    h->map_cap = n;
+  }
+  int rc = upload_params(h, beta, Delta, V, J);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h->d_maps, pairs, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaEventRecord(h->map_ev, h->stream));
+  for (int64_t k = 0; k < nmaps; ++k)
+    CK(launch_map(h->g, h->d_maps + 2 * P * k, P, (uint64_t)(map0 + k), h->t, h->stream));
+  // the caller may reuse `pairs` once the copy has run
+  CK(cudaEventSynchronize(h->map_ev));
+  return CCMC_OK;
 }
 
 int ccmc_observables(ccmc_lattice *h, ccmc_obs *out) {
