@@ -66,6 +66,10 @@ def lib():
             "oracle_map_build": (c_int, [c_int, c_int, c_uint64, c_int64, i32p]),
             "oracle_map_sweeps": (c_int64, [u8p, c_int, c_int, c_uint64, c_int64, c_int64,
                                             c_double, c_double, c_double, c_double, c_int, i64p]),
+            "oracle_penalty_sweeps": (c_int64, [u8p, c_int, c_int, c_uint64, c_int64, c_int64,
+                                                c_double, c_double, c_double, c_double, c_double,
+                                                POINTER(c_double), c_double, c_int, i64p,
+                                                POINTER(c_double)]),
             "oracle_enumerate": (c_int64, [c_int, c_int, c_int, i64p, i64p, i64p, i64p]),
         }
         for name, (res, args) in sig.items():
@@ -221,6 +225,23 @@ def map_sweeps(st: np.ndarray, seed: int, map0: int, nmaps: int, beta: float, De
     if n < 0:
         raise MemoryError("oracle allocation failed")
     return rec[:n]
+
+
+def penalty_sweeps(st: np.ndarray, seed: int, sweep0: int, nsweeps: int, beta: float,
+                   Delta: float, V: float, J: float, n: float, mu: float, kappa: float,
+                   obs_every: int = 1):
+    """Penalty-function baseline (Sec. 2.2) on ``st`` in place: single-site
+    Metropolis with -mu sum S, mu adjusted after every sweep.  Returns
+    (records, mu after every sweep)."""
+    Ly, Lx = st.shape
+    nrec_max = nsweeps // obs_every + 1 if obs_every > 0 else 0
+    rec = np.zeros((max(nrec_max, 1), REC), dtype=np.int64)
+    trace = np.zeros(max(nsweeps, 1), dtype=np.float64)
+    m = c_double(mu)
+    k = lib().oracle_penalty_sweeps(_u8(st), Lx, Ly, seed & ((1 << 64) - 1), sweep0, nsweeps,
+                                    beta, Delta, V, J, n, ctypes.byref(m), kappa, obs_every,
+                                    _p(rec, c_int64), _p(trace, c_double))
+    return rec[:k], trace[:nsweeps]
 
 
 def enumerate_dos(Lx: int, Ly: int, Q: int):

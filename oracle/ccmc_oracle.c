@@ -605,3 +605,68 @@ int64_t oracle_map_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t ma
   free(table);
   return nrec;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Penalty-function baseline (Sec. 2.2): the charge is held near nN not by the
+ * move but by a chemical-potential term -mu sum_i S_i added to the energy, with
+ * mu adjusted as the run goes.  Single-site Metropolis: a uniformly chosen site
+ * takes one of its three other states, uniformly, accepted with probability
+ * min(1, exp(-beta (dE - mu dS))), N proposals per sweep.  The paper gives no
+ * rule for adjusting mu; reading: after every sweep
+ *   mu <- mu + kappa (n N - sum_i S_i) / N.
+ * Random words: Philox(seed, (t_lo, t_hi, 0, PENALTY)) for proposal t: words
+ * 0-1 the site (Lemire over N, rejection), word 2 mod 3 the new state (word 2
+ * below 4294967295, a multiple of 3; else the proposal is skipped), word 3 the
+ * acceptance test (u / 2^32 < p).  Records as in the other modes; mu_trace
+ * (if not NULL) receives mu after every sweep. */
+int64_t oracle_penalty_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
+                              int64_t nsweeps, double beta, double Delta, double V, double J,
+                              double n, double *mu, double kappa, int obs_every,
+                              int64_t *records, double *mu_trace) {
+  uint32_t key[2];
+  seed_key(seed, key);
+  uint64_t N = (uint64_t)Lx * (uint64_t)Ly;
+  uint64_t reject_below = (0 - N) % N;
+  int64_t Ssum = 0;
+  for (uint64_t i = 0; i < N; ++i) Ssum += CODE_S[st[i]];
+  int64_t nrec = 0;
+  for (int64_t s = 0; s < nsweeps; ++s) {
+    int64_t sweep = sweep0 + s;
+    for (uint64_t mv = 0; mv < N; ++mv) {
+      uint64_t t = (uint64_t)sweep * N + mv;
+      uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), 0u, ORACLE_TAG_PENALTY};
+      uint32_t w[4];
+      oracle_philox4x32_10(ctr, key, w);
+      uint64_t x = ((uint64_t)w[1] << 32) | (uint64_t)w[0];
+      unsigned __int128 prod = (unsigned __int128)x * (unsigned __int128)N;
+      if ((uint64_t)prod < reject_below || w[2] == 0xFFFFFFFFu) continue;
+      int a = (int)(uint64_t)(prod >> 64);
+      int c = st[a];
+      int nc = (c + 1 + (int)(w[2] % 3u)) & 3;
+      int nbr[4];
+      neighbours(Lx, Ly, a, nbr);
+      int sumS = 0, sumG = 0;
+      for (int k = 0; k < 4; ++k) {
+        sumS += CODE_S[st[nbr[k]]];
+        sumG += CODE_SIGMA[st[nbr[k]]];
+      }
+      int dS = CODE_S[nc] - CODE_S[c];
+      int dQ = CODE_S[nc] * CODE_S[nc] - CODE_S[c] * CODE_S[c];
+      int dG = CODE_SIGMA[nc] - CODE_SIGMA[c];
+      double dE = Delta * dQ + V * (double)(dS * sumS) + 0.25 * J * (double)(dG * sumG);
+      double dEp = dE - *mu * (double)dS;
+      int accept = dEp <= 0.0 || ((double)w[3] * 0x1p-32) < exp(-beta * dEp);
+      if (accept) {
+        st[a] = (uint8_t)nc;
+        Ssum += dS;
+      }
+    }
+    *mu += kappa * (n * (double)N - (double)Ssum) / (double)N;
+    if (mu_trace) mu_trace[s] = *mu;
+    if (obs_every > 0 && (sweep + 1) % obs_every == 0 && records) {
+      write_record(st, Lx, Ly, sweep + 1, records + ORACLE_REC * nrec);
+      ++nrec;
+    }
+  }
+  return nrec;
+}

@@ -41,6 +41,7 @@ extern "C" {
 #define ORACLE_TAG_MAP 10u    /* paper maps: random-marking site draws      */
 #define ORACLE_TAG_MAPMOVE 11u /* paper maps: per pair, choice | u_hi       */
 #define ORACLE_TAG_MAPSLOW 12u /* paper maps: per pair, slow words          */
+#define ORACLE_TAG_PENALTY 13u /* penalty-function baseline: single sites   */
 
 /* Threshold table: dQ in [-2,2], dBV and dBJ in [-ORACLE_DB, ORACLE_DB]. */
 #define ORACLE_DB 24
@@ -124,6 +125,14 @@ int oracle_map_build(int Lx, int Ly, uint64_t seed, int64_t m, int32_t *pairs);
 int64_t oracle_map_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t map0, int64_t nmaps,
                           double beta, double Delta, double V, double J, int obs_every,
                           int64_t *records);
+
+/* Penalty-function baseline (Sec. 2.2): single-site Metropolis with the extra
+ * energy -mu sum S, mu <- mu + kappa (nN - sum S)/N after every sweep (the
+ * adjustment rule is this oracle's reading).  *mu is read and updated. */
+int64_t oracle_penalty_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
+                              int64_t nsweeps, double beta, double Delta, double V, double J,
+                              double n, double *mu, double kappa, int obs_every,
+                              int64_t *records, double *mu_trace);
 
 /* Exact enumeration of the states with sum S = Q (N <= 16): histogram over
  * (Nc, BV, BJ) with bins [Nc][BV + 2N][BJ + 2N] of size (N+1) x (4N+1) x (4N+1);

@@ -1,0 +1,47 @@
+"""The thermodynamics pipeline end to end on the GPU (one ccmc batch over a
+temperature grid with replicas): the paper's own 4 x 4 test against exact
+enumeration -- low-temperature heat-capacity peak included -- and the Ising
+limit of Eq. (3) on 8 x 8 against the transfer matrix."""
+import numpy as np
+import pytest
+
+from oracle.ising_tm import ising_energy_and_heat
+
+from .test_thermo_stats import _exact
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def thermo():
+    from paper_2301_11735_gb300 import thermo
+
+    return thermo
+
+
+def test_pipeline_matches_exact_enumeration_4x4(thermo):
+    Q, Delta, V, J = 2, -0.5, 1.0, 1.0
+    temps = [0.25, 0.6, 1.6, 3.0]
+    out = thermo.thermodynamics(4, temps, replicas=8, Delta=Delta, V=V, J=J, n=Q / 16,
+                                seed=7, equil_sweeps=2000, meas_sweeps=30000)
+    for i, T in enumerate(temps):
+        ex = _exact(Q, T, Delta, V, J)
+        for k in ("E", "C", "chi", "Nc"):
+            v, e = out[k][i], out[k + "_err"][i]
+            assert e > 0
+            assert abs(v - ex[k]) <= 4 * e + 1e-9, (T, k, v, ex[k], e)
+    # the low-temperature peak of C (Sec. 3.2) is resolved
+    assert out["C"][0] > 5 * out["C_err"][0]
+
+
+def test_pipeline_ising_limit_8x8(thermo):
+    J = 1.0
+    temps = [0.45, 0.6, 0.9]
+    # no charges and a charge gap of 2 Delta = 40: every site stays magnetic
+    out = thermo.thermodynamics(8, temps, replicas=8, Delta=20.0, V=1.0, J=J, counts=(0, 0),
+                                seed=3, equil_sweeps=2000, meas_sweeps=30000)
+    assert np.all(out["Nc"] == 0)
+    for i, T in enumerate(temps):
+        e, c = ising_energy_and_heat(8, T, J)
+        assert abs(out["E"][i] - e) <= 4 * out["E_err"][i], (T, out["E"][i], e)
+        assert abs(out["C"][i] - c) <= 4 * out["C_err"][i], (T, out["C"][i], c)

@@ -12,7 +12,9 @@ Eq. (2).  Checked against:
 * colour schedule vs sequential random pairs on 8 x 8;
 * a negative control: nearest-neighbour partners only (the paper's abandoned
   first version, Sec. 3.2) miss the low-temperature heat-capacity peak of
-  4 x 4 that the colour schedule reproduces.
+  4 x 4 that the colour schedule reproduces;
+* the penalty-function baseline (Sec. 2.2): a chemical-potential term holds
+  the charge only on average, and its heat capacity diverges as T -> 0.
 
 Means are compared within 4 standard errors from batch means.
 """
@@ -238,3 +240,31 @@ def test_short_range_pairs_agree_at_high_temperature():
     rec = oracle.sweeps(st, 9, 0, 200000, 1.0 / T, Delta, V, J, obs_every=1,
                         neighbour=True)[2000:]
     compare(rec, exact_averages(4, 4, Q, T, Delta, V, J), 16, T, Delta, V, J)
+
+
+def test_penalty_function_heat_capacity_diverges_as_t_goes_to_zero():
+    """Baseline of Sec. 2.2: holding the charge with a chemical-potential term
+    -mu sum S (mu adjusted after every sweep) instead of coupled pairs.  The
+    charge sum averages nN but keeps fluctuating, so the energy variance stays
+    finite as T -> 0 and C = var(E) / (N T^2) grows like 1/T^2 -- the failure
+    that led the paper to coupled pairs -- while the coupled-pair chain holds
+    sum S = nN exactly and follows the exact C(T) to zero."""
+    Q, Delta, V, J = 2, -0.5, 1.0, 1.0
+    C = {}
+    for T in (0.1, 0.25):
+        st = oracle.init_counts(4, 4, 5, 5, 3)
+        rec, mu = oracle.penalty_sweeps(st, 5, 0, 60000, 1.0 / T, Delta, V, J, Q / 16, 0.0, 0.5)
+        rec = rec[5000:]
+        S = rec[:, 6]
+        assert abs(S.mean() - Q) < 0.1 and S.std() > 1.0  # held on average only
+        C[T], _ = batch_heat(energy(rec, Delta, V, J), 16, T)
+        assert C[T] * T * T > 1.0  # the energy variance per site does not vanish
+        ex = exact_averages(4, 4, Q, T, Delta, V, J)["C"]
+        assert C[T] > 100 * ex
+    assert C[0.1] > 4 * C[0.25]
+    # the coupled-pair chain at the same point: charge fixed, C tiny and exact
+    st = oracle.init_counts(4, 4, 5, 5, 3)
+    rec = oracle.sweeps(st, 5, 0, 60000, 10.0, Delta, V, J, obs_every=1)[2000:]
+    assert np.all(rec[:, 6] == Q)
+    c, _ = batch_heat(energy(rec, Delta, V, J), 16, 0.1)
+    assert exact_averages(4, 4, Q, 0.1, Delta, V, J)["C"] < 0.01 and c < 0.01
