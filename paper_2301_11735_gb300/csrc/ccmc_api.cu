@@ -282,14 +282,17 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
     return fail(CCMC_E_NOMEM);
   const size_t tb = sizeof(uint32_t) * (kTableN + 4 * kTransN + kThrHiWords);
   if (cudaMalloc(&h->d_tables, tb) != cudaSuccess) return fail(CCMC_E_NOMEM);
+  // thrhi, trans_far and trans_near one after another (kStagedTableBytes, a
+  // multiple of 16 from a 256-byte aligned base): the tile kernel copies them
+  // into shared memory with one bulk copy; thr32 after them
   char *p = (char *)h->d_tables;
-  h->t.thr32 = (uint32_t *)p;
-  p += sizeof(uint32_t) * kTableN;
+  h->t.thrhi = (uint32_t *)p;
+  p += sizeof(uint32_t) * kThrHiWords;
   h->t.trans_far = (uint32_t *)p;
   p += sizeof(uint32_t) * 2 * kTransN;
   h->t.trans_near = (uint32_t *)p;
   p += sizeof(uint32_t) * 2 * kTransN;
-  h->t.thrhi = (uint32_t *)p;
+  h->t.thr32 = (uint32_t *)p;
   g.words = h->d_words;
   g.ctl = h->d_ctl;
   uint32_t tf[2 * kTransN], tn[2 * kTransN];

@@ -4,6 +4,7 @@
 // (declared in ccmc_internal.h).
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 
 #include "ccmc_count.cuh"
@@ -316,28 +317,44 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *th
 // ----------------------------------------------------------------------------
 // Tile-staged phase (lattices whose class rows are W words with W dividing 256
 // and a multiple of 4, and Cy a multiple of R = 256 / W).  A tile is R
-// consecutive rows of the a-class (256 words, one per thread).  One thread
-// stages the tile's ten row bands -- the a rows, the b rows and the rows of
-// all eight neighbour classes, each band R full rows -- into shared memory with
-// bulk asynchronous copies that complete on an mbarrier.  Three buffers rotate:
-// while a tile is evaluated, the next one is already staged and the previous
-// one's a and b bands are going back to global memory with bulk copies, so a
-// tile costs one block barrier.  No two tiles of a phase write the same rows
-// (each b row is the partner row of exactly one a row), and no tile reads a
-// row another tile writes (the pairs of a phase do not interact), so global
-// memory sees no atomics and staging may run ahead of the write-back.
+// consecutive rows of the a-class (256 words, one per thread).  Thread 0 stages
+// a tile's ten row bands -- the a rows, the b rows and the rows of all eight
+// neighbour classes, each band R full rows -- into shared memory with bulk
+// asynchronous copies that complete on the buffer's `full` mbarrier; the
+// threads evaluate their words from shared memory; each warp then arrives on
+// the buffer's `done` mbarrier and goes on to the next tile without waiting for
+// the other warps.  One tile later thread 0 waits for `done`, sends the tile's
+// a and b bands back with bulk copies, and stages the next tile into the buffer
+// whose write-back has finished reading it.  Three buffers rotate: tile k is
+// evaluated while tile k - 1 goes back and tile k + 1 arrives.  (Waiting for
+// `done` right after its own word, to stage two tiles ahead, measured slower:
+// thread 0's warp then trails the slowest warp every tile.)  No two tiles of
+// a phase write the same rows (each b row is the partner row of exactly one a
+// row), and no tile reads a row another tile writes (the pairs of a phase do
+// not interact), so global memory sees no atomics and staging may run ahead of
+// the write-back.
 constexpr int kTileWords = 256;
 constexpr int kBands = 10;
 constexpr int kTileBufs = 3;
+constexpr int kTileWarps = kTileWords / 32;
 constexpr int kWaitSpins = 1 << 20;  // bounded mbarrier waits
 
+// The lattice's threshold tops and both move tables, contiguous in device
+// memory (thrhi, trans_far, trans_near), staged with one bulk copy.
+constexpr uint32_t kStagedTableBytes = 4u * (kThrHiWords + 4 * kTransN);
+static_assert(kStagedTableBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+
 struct TileSmem {
-  uint32_t thrhi[kThrHiWords];
-  uint2 trans[kTransN];
+  alignas(128) uint32_t thrhi[kThrHiWords];
+  uint2 trans[2][kTransN];  // far, near: directly after thrhi, as in device memory
   alignas(128) uint32_t band[kTileBufs][kBands][kTileWords];
-  alignas(8) unsigned long long mbar[kTileBufs];
+  alignas(8) unsigned long long full[kTileBufs];  // bands landed (transaction count)
+  alignas(8) unsigned long long done[kTileBufs];  // every warp finished the tile
+  alignas(8) unsigned long long tables;           // the tables landed
   Sched sched;
   int err;
+  unsigned staged;  // thread 0: buffers whose bulk loads it has not waited for
+  unsigned dpar;    // thread 0, bit b: parity of the phase of done[b] waited for next
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -381,6 +398,10 @@ struct Band {
   int dy;  // first row relative to the tile's first a row
 };
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_t *thrhi,
                                                             const uint32_t *thr32,
                                                             const uint32_t *trans_far,
@@ -388,12 +409,23 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
                                                             int64_t p_off) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
   TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem);
-  for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) sm.thrhi[t] = thrhi[t];
+  static_assert(offsetof(TileSmem, trans) == 4 * kThrHiWords, "tables staged as one block");
   if (threadIdx.x == 0) {
     sm.err = 0;
-    for (int b = 0; b < kTileBufs; ++b)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar[b])));
+    for (int b = 0; b < kTileBufs; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.done[b])),
+                   "r"(kTileWarps));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.tables)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // The tables come from host uploads that precede the whole launch chain:
+    // their copy may start before the previous kernel of the stream finishes.
+    const uint32_t bar = smem_u32(&sm.tables);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(kStagedTableBytes)
+                 : "memory");
+    bulk_load(smem_u32(sm.thrhi), thrhi, kStagedTableBytes, bar);
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
@@ -404,9 +436,7 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
   }
   __syncthreads();
   const Sched sc = sm.sched;
-  const uint32_t *trans = sc.near ? trans_near : trans_far;
-  for (int t = threadIdx.x; t < kTransN; t += blockDim.x)
-    sm.trans[t] = make_uint2(trans[2 * t], trans[2 * t + 1]);
+  const uint2 *trans = sm.trans[sc.near ? 1 : 0];
   const PhaseU u = phase_uniform(g, sc);
   const int W = g.W, R = kTileWords / W, Cy = g.Cy;
   const Band bands[kBands] = {{u.cA, 0},          {u.cAL, 0},          {u.cAR, 0},
@@ -418,7 +448,7 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
 
   // thread 0 stages tile `tile` into buffer `buf`
   auto stage = [&](int tile, int buf) {
-    const uint32_t bar = smem_u32(&sm.mbar[buf]);
+    const uint32_t bar = smem_u32(&sm.full[buf]);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                  "r"((uint32_t)(kBands * kTileWords * 4))
                  : "memory");
@@ -432,30 +462,67 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
       if (n1 < R) bulk_load(dst + (uint32_t)n1 * row_bytes, bands[k].cls, (uint32_t)(R - n1) * row_bytes, bar);
     }
   };
+  // thread 0 sends the a and b bands of tile `tile` (buffer `buf`) back
+  auto write_back = [&](int tile, int buf) {
+    const int j0 = tile * R;
+    bulk_store(const_cast<uint32_t *>(u.cA) + (int64_t)j0 * W, smem_u32(&sm.band[buf][0][0]),
+               (uint32_t)R * row_bytes);
+    int rb = (j0 + u.qy) % Cy;
+    if (rb < 0) rb += Cy;
+    const int n1 = min(R, Cy - rb);
+    const uint32_t src = smem_u32(&sm.band[buf][5][0]);
+    bulk_store(const_cast<uint32_t *>(u.cB) + (int64_t)rb * W, src, (uint32_t)n1 * row_bytes);
+    if (n1 < R)
+      bulk_store(const_cast<uint32_t *>(u.cB), src + (uint32_t)n1 * row_bytes,
+                 (uint32_t)(R - n1) * row_bytes);
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  };
 
-  // thread 0: buffers whose copies are in flight and not yet waited for
-  unsigned staged = 0u;
   if (threadIdx.x == 0) {
-    for (int k = 0; k < 2; ++k) {
-      const int t = blockIdx.x + k * gridDim.x;
-      if (t < ntiles) {
-        stage(t, k);
-        staged |= 1u << k;
-      }
+    sm.staged = 0u;
+    sm.dpar = 0u;
+    if (blockIdx.x < (unsigned)ntiles) {
+      stage(blockIdx.x, 0);
+      sm.staged = 1u;
     }
   }
-  __syncthreads();  // the move table and the mbarrier initialisation
+  __syncthreads();  // the mbarrier initialisation
+  if (!mbar_wait(smem_u32(&sm.tables), 0u)) sm.err = 1;
 
   const int lw = __ffs(W) - 1;  // W is a power of two
   const int jr = threadIdx.x >> lw, w = threadIdx.x & (W - 1);
-  uint32_t par = 0u;  // bit b: parity of the phase of mbar[b] waited for next
-  int buf = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const bool ok = mbar_wait(smem_u32(&sm.mbar[buf]), (par >> buf) & 1u);
-    par ^= 1u << buf;
+  const bool lane0 = (threadIdx.x & 31) == 0;
+  uint32_t fpar = 0u;  // bit b: parity of the phase of full[b] waited for next
+  int buf = 0, k = 0;
+  int tile = blockIdx.x;
+  for (; tile < ntiles; tile += gridDim.x, ++k) {
+    if (threadIdx.x == 0) {
+      // (1) stage the next tile into the buffer of tile k - 2, whose
+      // write-back (issued one tile ago, the only copies outstanding) must
+      // have finished reading it
+      const int next = tile + gridDim.x;
+      if (next < ntiles) {
+        const int nb = buf == kTileBufs - 1 ? 0 : buf + 1;
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        stage(next, nb);
+        sm.staged |= 1u << nb;
+      }
+      // (2) send tile k - 1 back once every warp is done with it
+      if (k >= 1) {
+        const int pb = buf == 0 ? kTileBufs - 1 : buf - 1;
+        if (mbar_wait(smem_u32(&sm.done[pb]), (sm.dpar >> pb) & 1u)) {
+          sm.dpar ^= 1u << pb;
+          write_back(tile - gridDim.x, pb);
+        } else {
+          sm.err = 1;
+        }
+      }
+    }
+    // (3) evaluate this thread's word of tile k
+    const bool ok = mbar_wait(smem_u32(&sm.full[buf]), (fpar >> buf) & 1u);
+    fpar ^= 1u << buf;
     if (ok) {
-      if (threadIdx.x == 0) staged &= ~(1u << buf);
-      // evaluate this thread's word from the staged bands
+      if (threadIdx.x == 0) sm.staged &= ~(1u << buf);
       const uint32_t *base = sm.band[buf][0];
       PhaseU lu = u;
       lu.cA = base;
@@ -468,45 +535,34 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
       lu.cBR = base + 7 * kTileWords;
       lu.cBU = base + 8 * kTileWords;
       lu.cBD = base + 9 * kTileWords;
-      phase_word<kRowTile>(g, lu, sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P);
+      phase_word<kRowTile>(g, lu, trans, sm.thrhi, thr32, tile * R + jr, jr, w, P);
     } else {
       sm.err = 1;
     }
-    __syncthreads();
-    if (sm.err) break;
-    if (threadIdx.x == 0) {
-      // write the a and b bands back
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      const int j0 = tile * R;
-      bulk_store(const_cast<uint32_t *>(u.cA) + (int64_t)j0 * W, smem_u32(&sm.band[buf][0][0]),
-                 (uint32_t)R * row_bytes);
-      int rb = (j0 + u.qy) % Cy;
-      if (rb < 0) rb += Cy;
-      const int n1 = min(R, Cy - rb);
-      const uint32_t src = smem_u32(&sm.band[buf][5][0]);
-      bulk_store(const_cast<uint32_t *>(u.cB) + (int64_t)rb * W, src, (uint32_t)n1 * row_bytes);
-      if (n1 < R)
-        bulk_store(const_cast<uint32_t *>(u.cB), src + (uint32_t)n1 * row_bytes,
-                   (uint32_t)(R - n1) * row_bytes);
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-      // stage the tile after next into the buffer evaluated one tile ago, once
-      // its write-back (committed one tile ago) has read it
-      const int next2 = tile + 2 * gridDim.x;
-      if (next2 < ntiles) {
-        const int nb = buf == 0 ? kTileBufs - 1 : buf - 1;
-        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-        stage(next2, nb);
-        staged |= 1u << nb;
-      }
-    }
+    // this thread's shared-memory writes become visible to the bulk copies
+    // after the `done` handshake
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane0) mbar_arrive(smem_u32(&sm.done[buf]));
     buf = buf == kTileBufs - 1 ? 0 : buf + 1;
+    // leave together: the warp's lanes meet in __syncwarp every tile
+    if (__any_sync(0xFFFFFFFFu, *(volatile int *)&sm.err != 0)) break;
   }
   if (threadIdx.x == 0) {
+    if (!sm.err && k >= 1) {
+      // the last tile
+      const int pb = buf == 0 ? kTileBufs - 1 : buf - 1;
+      if (mbar_wait(smem_u32(&sm.done[pb]), (sm.dpar >> pb) & 1u))
+        write_back(tile - gridDim.x, pb);
+      else
+        sm.err = 1;
+    }
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (sm.err) {
-      // give copies still in flight a bounded chance to land before exiting
+      // give loads still in flight a bounded chance to land before exiting
+      mbar_wait(smem_u32(&sm.tables), 0u);
       for (int b = 0; b < kTileBufs; ++b)
-        if (staged & (1u << b)) mbar_wait(smem_u32(&sm.mbar[b]), (par >> b) & 1u);
+        if (sm.staged & (1u << b)) mbar_wait(smem_u32(&sm.full[b]), (fpar >> b) & 1u);
       g.ctl[kCtlStatus] = 1;
     }
   }
@@ -715,6 +771,9 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
   if (cfg.tile_grid > 0) {
     const int64_t tiles = nw / kTileWords;
     const int grid = (int)(tiles < cfg.tile_grid ? tiles : cfg.tile_grid);
+    if (t.trans_far != t.thrhi + kThrHiWords || t.trans_near != t.trans_far + 2 * kTransN ||
+        (reinterpret_cast<uintptr_t>(t.thrhi) & 15u))
+      return cudaErrorInvalidValue;  // the tables must be one staged block
     return launch_pdl_smem(phase_tile_kernel, grid, 256, sizeof(TileSmem), s, g, t.thrhi,
                            t.thr32, t.trans_far, t.trans_near, p_off);
   }

@@ -22,8 +22,11 @@ def thermo():
 def test_pipeline_matches_exact_enumeration_4x4(thermo):
     Q, Delta, V, J = 2, -0.5, 1.0, 1.0
     temps = [0.25, 0.6, 1.6, 3.0]
+    # C at T = 0.6 comes from rare excitations: short runs undershoot it with
+    # errors that do not show it (30000 sweeps a replica: 5 sigma low), so
+    # each replica runs 200000 sweeps
     out = thermo.thermodynamics(4, temps, replicas=8, Delta=Delta, V=V, J=J, n=Q / 16,
-                                seed=7, equil_sweeps=2000, meas_sweeps=30000)
+                                seed=7, equil_sweeps=2000, meas_sweeps=200000, obs_every=2)
     for i, T in enumerate(temps):
         ex = _exact(Q, T, Delta, V, J)
         for k in ("E", "C", "chi", "Nc"):
