@@ -11,11 +11,13 @@ Timing: W warm-up steps, then K timed steps, each bracketed by CUDA events on
 the issuing stream; L2 is flushed (a 256 MB write)
 between timed steps, outside the events.  nvidia-smi samples clocks during the
 timed region.  `e2e` repeats the steps through the C ABI with host buffers:
-every step uploads the four lattices from pinned host memory (ccmc_set_state)
-and reads the observable records back (ccmc_obs_series).
+every step uploads the lattices from pinned host memory in the compact form,
+2 bits a site (ccmc_set_state_packed, stream-ordered), and reads the
+observable records back (ccmc_obs_series).
 
-Beside the headline the same JSON line carries two more measurements of the
-spec patterns: `batched` (512 replicas of uneven L in one persistent
+Beside the headline the same JSON line carries more measurements of the
+spec patterns: `paper_maps` (the paper's own host-built maps against the
+colour schedule), `batched` (512 replicas of uneven L in one persistent
 launch, against back-to-back single-lattice launches) and `served` (a Poisson
 request stream through the continuous-batching server: p50/p99 latency,
 achieved vs offered site-updates/s, against back-to-back plain runs).
@@ -488,10 +490,13 @@ def run_ours(args):
         issue = {"warp_inst_per_launch": counters["warp_inst"], "achieved": rate,
                  "peak": peak_issue, "unit": "warp-inst/s", "frac": rate / peak_issue}
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: every step uploads each
+    # lattice's state in the compact form (2 bits a site) from pinned host
+    # memory, stream-ordered so that one lattice's upload overlaps the others'
+    # sweeps, and reads the records back
     host_states = []
     for lat in lats:
-        h = torch.from_numpy(lat.get_state()).pin_memory()
+        h = torch.from_numpy(lat.get_state_packed()).pin_memory()
         host_states.append(h)
     rec_bytes = 0
     e2e_times = []
@@ -499,7 +504,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for lat, s, h in zip(lats, sims, host_states):
-            lat.set_state_ptr(h.data_ptr(), s.seed, 0)
+            lat.set_state_packed_ptr(h.data_ptr(), s.seed, 0)
         batch.sweep(STEP_SWEEPS, *cols, obs_every=sims[0].obs_every)
         recs = [lat.obs_series(cap=16) for lat in lats]
         dt = time.perf_counter() - t0

@@ -198,6 +198,24 @@ int ccmc_get_state(ccmc_lattice *h, uint8_t *host_out);
  * bit for bit.  Errors: E_INVAL (code > 3). */
 int ccmc_set_state(ccmc_lattice *h, const uint8_t *host_in, uint64_t seed, int64_t sweeps_done);
 
+/* Compact state, 2 bits a site in row-major order: site i = y * Lx + x is
+ * the code (as in ccmc_get_state) at bits 2 (i mod 4) .. 2 (i mod 4) + 1 of
+ * byte i / 4; Lx * Ly / 4 bytes (Lx is a multiple of 4, so each row is Lx / 4
+ * whole bytes).  A quarter of the byte-per-site form: for checkpoints and for
+ * streaming lattices in and out of the GPU.
+ *
+ * ccmc_get_state_packed: host-returning (synchronises the lattice's stream).
+ * ccmc_set_state_packed: stream-ordered, it returns once the work is queued
+ * on the lattice's stream; the copy reads host_in later, so the buffer must
+ * stay valid and unchanged until the next call that synchronises the lattice
+ * (ccmc_sync, ccmc_observables, ccmc_get_state...).  Every byte is a valid
+ * input (all four 2-bit codes are states).  seed and sweeps_done as in
+ * ccmc_set_state.  Errors: E_INVAL, E_STATE (get before any state), E_NOMEM,
+ * E_CUDA. */
+int ccmc_get_state_packed(ccmc_lattice *h, uint8_t *host_out);
+int ccmc_set_state_packed(ccmc_lattice *h, const uint8_t *host_in, uint64_t seed,
+                          int64_t sweeps_done);
+
 /* Block until the handle's queued work is done; reports a device-side error. */
 int ccmc_sync(ccmc_lattice *h);
 

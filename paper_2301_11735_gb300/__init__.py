@@ -85,6 +85,8 @@ def _load():
         "ccmc_hist_get": (c_int, [vp, i64p]),
         "ccmc_get_state": (c_int, [vp, u8p]),
         "ccmc_set_state": (c_int, [vp, u8p, c_uint64, c_int64]),
+        "ccmc_get_state_packed": (c_int, [vp, u8p]),
+        "ccmc_set_state_packed": (c_int, [vp, u8p, c_uint64, c_int64]),
         "ccmc_sync": (c_int, [vp]),
         "ccmc_philox_device": (c_int, [c_uint32] * 6 + [c_int64, u32p]),
         "ccmc_batch_create": (c_int, [c_int, POINTER(vp), vp, POINTER(vp)]),
@@ -267,6 +269,30 @@ class Lattice:
         """set_state from a raw host pointer to Lx * Ly site codes (e.g. pinned)."""
         _check(lib().ccmc_set_state(self._h, ctypes.cast(host_ptr, POINTER(ctypes.c_uint8)),
                                    seed & (2 ** 64 - 1), sweeps_done), "ccmc_set_state")
+
+    def get_state_packed(self) -> np.ndarray:
+        """The state in the compact form: Lx * Ly / 4 bytes, site y * Lx + x at
+        bits 2 ((y * Lx + x) mod 4) of byte (y * Lx + x) / 4."""
+        out = np.empty(self.Lx * self.Ly // 4, dtype=np.uint8)
+        _check(lib().ccmc_get_state_packed(self._h, out.ctypes.data_as(POINTER(ctypes.c_uint8))),
+               "ccmc_get_state_packed")
+        return out
+
+    def set_state_packed_ptr(self, host_ptr: int, seed: int, sweeps_done: int = 0):
+        """Queue a compact-state upload from a raw host pointer (e.g. pinned);
+        the buffer must stay valid until the next synchronising call."""
+        _check(lib().ccmc_set_state_packed(self._h, ctypes.cast(host_ptr,
+                                                                POINTER(ctypes.c_uint8)),
+                                           seed & (2 ** 64 - 1), sweeps_done),
+               "ccmc_set_state_packed")
+
+    def set_state_packed(self, packed: np.ndarray, seed: int, sweeps_done: int = 0):
+        """Queue a compact-state upload; the array is kept alive until sync()."""
+        packed = np.ascontiguousarray(packed, dtype=np.uint8)
+        if packed.size != self.Lx * self.Ly // 4:
+            raise ValueError("packed state must hold Lx * Ly / 4 bytes")
+        self._pending = packed
+        self.set_state_packed_ptr(packed.ctypes.data, seed, sweeps_done)
 
     def set_state(self, st: np.ndarray, seed: int, sweeps_done: int = 0):
         st = np.ascontiguousarray(st, dtype=np.uint8)

@@ -14,6 +14,7 @@
 #include "../../include/ccmc.h"
 #include "ccmc_internal.h"
 #include "ccmc_map.h"
+#include "ccmc_state.h"
 
 using namespace ccmc;
 
@@ -522,6 +523,35 @@ int ccmc_get_state(ccmc_lattice *h, uint8_t *host_out) {
   CK(launch_unpack(h->g, h->d_bytes, h->stream));
   CK(cudaMemcpyAsync(host_out, h->d_bytes, N, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return CCMC_OK;
+}
+
+int ccmc_get_state_packed(ccmc_lattice *h, uint8_t *host_out) {
+  if (!h || !host_out) return CCMC_E_INVAL;
+  if (!h->initialised) return CCMC_E_STATE;
+  int rc = ensure_bytes(h);
+  if (rc) return rc;
+  const size_t nb = (size_t)h->g.Lx * h->g.Ly / 4;
+  CK(launch_unpack2(h->g, h->d_bytes, h->stream));
+  CK(cudaMemcpyAsync(host_out, h->d_bytes, nb, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CCMC_OK;
+}
+
+int ccmc_set_state_packed(ccmc_lattice *h, const uint8_t *host_in, uint64_t seed,
+                          int64_t sweeps_done) {
+  if (!h || !host_in || sweeps_done < 0 || sweeps_done > ((int64_t)1 << 59)) return CCMC_E_INVAL;
+  int rc = ensure_bytes(h);
+  if (rc) return rc;
+  const size_t nb = (size_t)h->g.Lx * h->g.Ly / 4;
+  // every 2-bit code is a state: nothing to validate, nothing to wait for
+  CK(cudaMemcpyAsync(h->d_bytes, host_in, nb, cudaMemcpyHostToDevice, h->stream));
+  set_seed(h, seed);
+  CK(launch_pack2(h->g, h->d_bytes, h->stream));
+  CK(launch_set_ctl(h->d_ctl, 8 * sweeps_done, h->stream));
+  if (h->d_hist) CK(cudaMemsetAsync(h->d_hist, 0, sizeof(int64_t) * 3 * h->nbins, h->stream));
+  h->phases_done = 8 * sweeps_done;
+  h->initialised = true;
   return CCMC_OK;
 }
 

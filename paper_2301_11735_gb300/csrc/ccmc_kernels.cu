@@ -10,6 +10,7 @@
 #include "ccmc_device.cuh"
 #include "ccmc_internal.h"
 #include "ccmc_launch.cuh"
+#include "ccmc_state.h"
 
 namespace ccmc {
 
@@ -205,6 +206,81 @@ __global__ void pack_kernel(Geo g, const uint8_t *in, int *bad) {
   }
 }
 
+// Compact row-major state, 2 bits a site: site i = y Lx + x at bits 2 (i mod
+// 4) of byte i / 4.  As Lx is a multiple of 4, byte i of row y holds column i of
+// the four classes (cx = 0..3) of class row y / 4, y mod 4: one thread builds
+// (or splits) the four class words of column block w from 16 consecutive bytes.
+__device__ __forceinline__ uint32_t gather_field(uint32_t q, int cx) {
+  // the cx-th 2-bit field of each of q's four bytes, packed into 8 bits
+  uint32_t x = (q >> (2 * cx)) & 0x03030303u;
+  x = (x | (x >> 6)) & 0x000F000Fu;
+  return (x | (x >> 12)) & 0xFFu;
+}
+
+__device__ __forceinline__ uint32_t scatter_field(uint32_t f, int cx) {
+  // inverse of gather_field: 8 bits -> the cx-th field of four bytes
+  uint32_t x = (f | (f << 12)) & 0x000F000Fu;
+  x = (x | (x << 6)) & 0x03030303u;
+  return x << (2 * cx);
+}
+
+__global__ void pack2_kernel(Geo g, const uint8_t *in) {
+  const int64_t nthr = 4 * (int64_t)g.Cy * g.W;
+  const int64_t row_bytes = g.Lx / 4;
+  const bool vec = (row_bytes & 15) == 0;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < nthr;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int w = (int)(id % g.W);
+    const int64_t r = id / g.W;  // r = cy Cy + j
+    const int cy = (int)(r / g.Cy), j = (int)(r - (int64_t)cy * g.Cy);
+    const uint8_t *src = in + (int64_t)(4 * j + cy) * row_bytes + 16 * w;
+    const int n = min(16, g.Cx - 16 * w);
+    uint32_t q[4] = {0u, 0u, 0u, 0u};
+    if (vec) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(src);
+      q[0] = v.x;
+      q[1] = v.y;
+      q[2] = v.z;
+      q[3] = v.w;
+    } else {
+      for (int t = 0; t < n; ++t) q[t >> 2] |= (uint32_t)src[t] << (8 * (t & 3));
+    }
+#pragma unroll
+    for (int cx = 0; cx < 4; ++cx) {
+      uint32_t word = 0u;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) word |= gather_field(q[k], cx) << (8 * k);
+      g.words[(int64_t)(cy * 4 + cx) * g.cstride + (int64_t)j * g.W + w] = word;
+    }
+  }
+}
+
+__global__ void unpack2_kernel(Geo g, uint8_t *out) {
+  const int64_t nthr = 4 * (int64_t)g.Cy * g.W;
+  const int64_t row_bytes = g.Lx / 4;
+  const bool vec = (row_bytes & 15) == 0;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < nthr;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int w = (int)(id % g.W);
+    const int64_t r = id / g.W;
+    const int cy = (int)(r / g.Cy), j = (int)(r - (int64_t)cy * g.Cy);
+    uint8_t *dst = out + (int64_t)(4 * j + cy) * row_bytes + 16 * w;
+    const int n = min(16, g.Cx - 16 * w);
+    uint32_t q[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int cx = 0; cx < 4; ++cx) {
+      const uint32_t word = g.words[(int64_t)(cy * 4 + cx) * g.cstride + (int64_t)j * g.W + w];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q[k] |= scatter_field((word >> (8 * k)) & 0xFFu, cx);
+    }
+    if (vec) {
+      *reinterpret_cast<uint4 *>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
+    } else {
+      for (int t = 0; t < n; ++t) dst[t] = (uint8_t)(q[t >> 2] >> (8 * (t & 3)));
+    }
+  }
+}
+
 __global__ void philox_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                               uint32_t k1, int64_t count, uint32_t *out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
@@ -256,6 +332,16 @@ cudaError_t launch_unpack(const Geo &g, uint8_t *out, cudaStream_t s) {
 
 cudaError_t launch_pack(const Geo &g, const uint8_t *in, int *bad, cudaStream_t s) {
   pack_kernel<<<grid_for(16 * g.cstride, 256, 152 * 16), 256, 0, s>>>(g, in, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack2(const Geo &g, const uint8_t *in, cudaStream_t s) {
+  pack2_kernel<<<grid_for(4 * (int64_t)g.Cy * g.W, 256, 152 * 16), 256, 0, s>>>(g, in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack2(const Geo &g, uint8_t *out, cudaStream_t s) {
+  unpack2_kernel<<<grid_for(4 * (int64_t)g.Cy * g.W, 256, 152 * 16), 256, 0, s>>>(g, out);
   return cudaGetLastError();
 }
 

@@ -308,3 +308,30 @@ def test_tile_path_nearest_neighbour_phases(cc, want):
         st, rec = oracle_run(st, seed, 0, nsw, *params)
         assert np.array_equal(lat.get_state(), st), (want, seed, P)
         assert np.array_equal(lat.obs_series(), rec)
+
+
+def _pack_rowmajor(st):
+    """The compact form by its definition: site i at bits 2 (i mod 4) of byte i / 4."""
+    c = st.reshape(-1, 4).astype(np.uint8)
+    return (c[:, 0] | (c[:, 1] << 2) | (c[:, 2] << 4) | (c[:, 3] << 6)).astype(np.uint8)
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (12, 20), (64, 64), (68, 20), (260, 36), (256, 128),
+                                   (1024, 64)])
+def test_packed_state_roundtrip_and_resume(cc, shape):
+    Lx, Ly = shape
+    rng = np.random.default_rng(Lx + Ly)
+    st = rng.integers(0, 4, size=(Ly, Lx)).astype(np.uint8)
+    packed = _pack_rowmajor(st)
+    seed, params = 17 + Lx, (1.2, 0.2, 1.0, 0.5)
+    with cc.Lattice(Lx, Ly) as lat:
+        lat.set_state_packed(packed, seed, 3)
+        lat.sync()
+        assert np.array_equal(lat.get_state(), st)
+        assert np.array_equal(lat.get_state_packed(), packed)
+        lat.sweep(2, *params, obs_every=1)
+        got = lat.get_state()
+        rec = lat.obs_series()
+    exp, erec = oracle_run(st, seed, 3, 2, *params)
+    assert np.array_equal(got, exp), first_difference(got, exp)
+    assert np.array_equal(rec, erec)
