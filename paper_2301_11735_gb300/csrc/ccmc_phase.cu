@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
   uint2 *s_far = reinterpret_cast<uint2 *>(dyn + kThrHiWords);
   uint2 *s_near = s_far + kTransN;
   uint32_t *s_words = dyn + kResTableWords;
-  __shared__ Sched s_sched;
+  __shared__ Sched s_sched[8];  // the schedules of the current sweep's phases
   __shared__ int s_job;
   __shared__ int64_t s_red[32][7];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -657,15 +657,19 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
     const bool aligned = (g.Cx & 15) == 0;
     const int nwa = g.Cy * g.W;  // a-words per phase
     __syncthreads();
+    const int nwarps = blockDim.x >> 5;
     for (int64_t s = 0; s < nsweeps; ++s) {
+      // the eight schedules of the sweep depend on nothing but the phase
+      // index: the warps draw them together, then every phase needs only the
+      // barrier that orders it after the previous one
+      for (int q = warp; q < 8; q += nwarps) {
+        const Sched sc = draw_schedule(gs, (uint64_t)(P0 + 8 * s + q));
+        if (lane == 0) s_sched[q] = sc;
+      }
+      __syncthreads();
       for (int p = 0; p < 8; ++p) {
         const uint64_t P = (uint64_t)(P0 + 8 * s + p);
-        if (threadIdx.x < 32) {
-          const Sched sc = draw_schedule(gs, P);
-          if (threadIdx.x == 0) s_sched = sc;
-        }
-        __syncthreads();
-        const Sched sc = s_sched;
+        const Sched sc = s_sched[p];
         const PhaseU u = phase_uniform(gs, sc);
         const uint2 *tr = sc.near ? s_near : s_far;
         for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
