@@ -29,6 +29,7 @@ of the same workload.  Under torchrun each rank runs its own four lattices
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -175,6 +176,25 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def rank_sims(sims, rank: int):
+    """This rank's lattices under torchrun: the workload's, with seeds moved by
+    len(sims) * rank, so every rank sweeps its own, distinct lattices (weak
+    scaling; nothing on the data path crosses ranks)."""
+    return [dataclasses.replace(s, seed=s.seed + len(sims) * rank) for s in sims]
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """x maximised over the ranks of the process group (dist None: one rank);
+    the job's time is its slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def workload(name: str):
@@ -414,7 +434,7 @@ def run_ours(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     sims, workload_desc = workload(args.workload)
-    sims = [type(s)(**{**s.__dict__, "seed": s.seed + len(sims) * rank}) for s in sims]
+    sims = rank_sims(sims, rank)
     # explicit streams: one issuing stream for the timing events and the L2 flush,
     # one per lattice so that the four run concurrently (torch's default stream
     # has handle 0, which the library reads as "create your own")
@@ -459,13 +479,12 @@ def run_ours(args):
                 flush.zero_()
             evs.append(step())
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
     clocks = sampler.summary()
     updates_per_step = sum(s.sites for s in sims) * STEP_SWEEPS
     value = updates_per_step * args.steps * world / total_s
@@ -523,7 +542,8 @@ def run_ours(args):
         rec_bytes = sum(r.nbytes for r in recs)
         if k > 0:
             e2e_times.append(dt)
-    e2e_value = updates_per_step * len(e2e_times) * world / sum(e2e_times)
+    e2e_value = updates_per_step * len(e2e_times) * world / max_over_ranks(sum(e2e_times), dist,
+                                                                           "cuda")
 
     if rank == 0:
         line = {
