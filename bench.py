@@ -89,26 +89,36 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    """nvidia-smi clock and throttle samples every 50 ms.  Started before the
+    warm-up (nvidia-smi takes a moment to start); mark() brackets the timed
+    region and summary() keeps the samples whose timestamps fall inside it."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
+        self.window = [None, None]
         self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.file, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        # wait (at most 5 s) for the first sample
+        t0 = time.time()
+        while self.proc and time.time() - t0 < 5.0 and os.path.getsize(self.file.name) == 0:
+            time.sleep(0.02)
         return self
+
+    def mark(self, k: int):
+        self.window[k] = time.time()
 
     def __exit__(self, *exc):
         if self.proc:
@@ -119,23 +129,30 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        import datetime
+
         self.file.flush()
         self.file.seek(0)
         rows = [r.split(", ") for r in self.file.read().strip().splitlines() if r.strip()]
         os.unlink(self.file.name)
+        lo, hi = self.window
         sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             try:
-                sm.append(float(r[1]))
-                smax = max(smax, float(r[2]))
-                for name, v in zip(names, r[5:9]):
+                ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if lo is not None and hi is not None and not lo <= ts <= hi:
+                    continue
+                sm.append(float(r[2]))
+                smax = max(smax, float(r[3]))
+                for name, v in zip(names, r[6:10]):
                     if v.strip() == "Active":
                         reasons.add(name)
             except (ValueError, IndexError):
                 continue
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": smax or None, "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_max_mhz": smax or None, "reasons": sorted(reasons), "samples": len(sm),
+                "interval_ms": 50}
 
 
 def launches_per_call(nsweeps: int, obs_every: int, done: int) -> int:
@@ -464,16 +481,17 @@ def run_ours(args):
         ev1.record(main)
         return ev0, ev1
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     sampler = ClockSampler(local)
     evs = []
-    t_wall = time.perf_counter()
     with sampler:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler.mark(0)
+        t_wall = time.perf_counter()
         for _ in range(args.steps):
             with torch.cuda.stream(main):
                 flush.zero_()
@@ -482,7 +500,8 @@ def run_ours(args):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall
+        t_wall = time.perf_counter() - t_wall
+        sampler.mark(1)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_s = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
     clocks = sampler.summary()

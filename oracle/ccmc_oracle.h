@@ -128,7 +128,10 @@ int64_t oracle_map_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t ma
 
 /* Penalty-function baseline (Sec. 2.2): single-site Metropolis with the extra
  * energy -mu sum S, mu <- mu + kappa (nN - sum S)/N after every sweep (the
- * adjustment rule is this oracle's reading).  *mu is read and updated. */
+ * adjustment rule is this oracle's reading).  *mu is read and updated.
+ * Parity unpinned: a mu-controlled chain has no exact reference; its test
+ * checks the qualitative behaviour the paper reports (charge held on average
+ * only, heat capacity growing as T -> 0).  It has no GPU counterpart. */
 int64_t oracle_penalty_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
                               int64_t nsweeps, double beta, double Delta, double V, double J,
                               double n, double *mu, double kappa, int obs_every,
