@@ -281,26 +281,22 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
       cudaMalloc(&h->d_ring, sizeof(int64_t) * 8 * h->ring_cap) != cudaSuccess ||
       cudaMalloc(&h->d_flag, sizeof(int)) != cudaSuccess)
     return fail(CCMC_E_NOMEM);
-  const size_t tb = sizeof(uint32_t) * (kTableN + 4 * kTransN + kThrHiWords);
+  const size_t tb = sizeof(uint32_t) * (kTableN + 2 * kMoveN + kThrHiWords);
   if (cudaMalloc(&h->d_tables, tb) != cudaSuccess) return fail(CCMC_E_NOMEM);
-  // thrhi, trans_far and trans_near one after another (kStagedTableBytes, a
+  // thrhi and the move table one after another (kStagedTableBytes, a
   // multiple of 16 from a 256-byte aligned base): the tile kernel copies them
   // into shared memory with one bulk copy; thr32 after them
   char *p = (char *)h->d_tables;
   h->t.thrhi = (uint32_t *)p;
   p += sizeof(uint32_t) * kThrHiWords;
-  h->t.trans_far = (uint32_t *)p;
-  p += sizeof(uint32_t) * 2 * kTransN;
-  h->t.trans_near = (uint32_t *)p;
-  p += sizeof(uint32_t) * 2 * kTransN;
+  h->t.trans = (uint32_t *)p;
+  p += sizeof(uint32_t) * 2 * kMoveN;
   h->t.thr32 = (uint32_t *)p;
   g.words = h->d_words;
   g.ctl = h->d_ctl;
-  uint32_t tf[2 * kTransN], tn[2 * kTransN];
-  if (!build_transitions(tf, tn)) return fail(CCMC_E_INVAL);
-  if (cudaMemcpyAsync(h->t.trans_far, tf, sizeof(tf), cudaMemcpyHostToDevice, h->stream) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(h->t.trans_near, tn, sizeof(tn), cudaMemcpyHostToDevice, h->stream) !=
+  uint32_t tr[2 * kMoveN];
+  if (!build_transitions(tr)) return fail(CCMC_E_INVAL);
+  if (cudaMemcpyAsync(h->t.trans, tr, sizeof(tr), cudaMemcpyHostToDevice, h->stream) !=
           cudaSuccess ||
       cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t) * 16 * g.cstride, h->stream) !=
           cudaSuccess ||
@@ -614,8 +610,7 @@ JobDesc job_of(ccmc_lattice *h, int64_t nsweeps, int obs_every) {
   d.g = h->g;
   d.thrhi = h->t.thrhi;
   d.thr32 = h->t.thr32;
-  d.trans_far = h->t.trans_far;
-  d.trans_near = h->t.trans_near;
+  d.trans = h->t.trans;
   d.nsweeps = nsweeps;
   d.ring = h->d_ring;
   d.ring_cap = h->ring_cap;
@@ -690,8 +685,7 @@ int run_multi(ccmc_batch *b, MultiGroup &G, int64_t nsweeps, int obs_every) {
     j.g = h->g;
     j.thrhi = h->t.thrhi;
     j.thr32 = h->t.thr32;
-    j.trans_far = h->t.trans_far;
-    j.trans_near = h->t.trans_near;
+    j.trans = h->t.trans;
     j.cta_begin = begin;
     j.cta_count = share;
     begin += share;

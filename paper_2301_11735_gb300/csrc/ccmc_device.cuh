@@ -148,17 +148,35 @@ struct Sums {
   uint32_t se, so, ge, go;
 };
 
-__device__ __forceinline__ void add_neighbour(Sums &s, uint32_t X) {
-  const uint32_t K = (X >> 1) & 0x55555555u;  // charged
-  const uint32_t G = X & 0x55555555u;         // sign bit (1 = negative)
-  const uint32_t nK = ~K & 0x55555555u;
-  // S + 1 = 2 (S = +1), 1 (magnetic), 0 (S = -1); sigma + 1 likewise.
-  const uint32_t s1 = ((K & ~G) << 1) | nK;
-  const uint32_t g1 = ((nK & ~G) << 1) | K;
-  s.se += s1 & 0x33333333u;
-  s.so += (s1 >> 2) & 0x33333333u;
-  s.ge += g1 & 0x33333333u;
-  s.go += (g1 >> 2) & 0x33333333u;
+// Each window is first rewritten in the linear code (bit 1 = charged XOR
+// sign, bit 0 = sign), in which S = b1 - b0 and sigma = 1 - b1 - b0 hold for all
+// four states.  Two lane sums over the neighbours, c = sum (2 b1 + b0) and
+// n1 = sum b1, then give sum (S + 1) = 3 n1 - c + 4 and sum (sigma + 1) =
+// n1 - c + 8.  (Lane values may overflow in between; the 32-bit results are
+// exact because every final lane value lies in [0, 8].)
+__device__ __forceinline__ uint32_t linear_code(uint32_t X) {
+  return X ^ ((X << 1) & 0xAAAAAAAAu);
+}
+
+__device__ __forceinline__ Sums neighbour_sums(uint32_t X0, uint32_t X1, uint32_t X2,
+                                               uint32_t X3) {
+  const uint32_t Y0 = linear_code(X0), Y1 = linear_code(X1), Y2 = linear_code(X2),
+                 Y3 = linear_code(X3);
+  const uint32_t E0 = Y0 & 0x33333333u, E1 = Y1 & 0x33333333u, E2 = Y2 & 0x33333333u,
+                 E3 = Y3 & 0x33333333u;
+  const uint32_t O0 = (Y0 >> 2) & 0x33333333u, O1 = (Y1 >> 2) & 0x33333333u,
+                 O2 = (Y2 >> 2) & 0x33333333u, O3 = (Y3 >> 2) & 0x33333333u;
+  const uint32_t ce = E0 + E1 + E2 + E3, co = O0 + O1 + O2 + O3;
+  const uint32_t ne = ((E0 & 0x22222222u) + (E1 & 0x22222222u) + (E2 & 0x22222222u) +
+                       (E3 & 0x22222222u)) >> 1;
+  const uint32_t no = ((O0 & 0x22222222u) + (O1 & 0x22222222u) + (O2 & 0x22222222u) +
+                       (O3 & 0x22222222u)) >> 1;
+  Sums s;
+  s.se = 3u * ne + 0x44444444u - ce;
+  s.so = 3u * no + 0x44444444u - co;
+  s.ge = ne + 0x88888888u - ce;
+  s.go = no + 0x88888888u - co;
+  return s;
 }
 
 // Byte lanes of group k (sites k, k + 4, k + 8, k + 12) from 4-bit lanes.

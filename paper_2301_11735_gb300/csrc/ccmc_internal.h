@@ -47,13 +47,15 @@ struct Geo {
 struct DevTables {
   uint32_t *thrhi;      // kThrHiWords: each threshold with its low half cleared (fast path)
   uint32_t *thr32;      // kTableN: full thresholds (exact path)
-  uint32_t *trans_far;  // kTransN x 2 words: move entries, partner not a neighbour
-  uint32_t *trans_near; // kTransN x 2 words: move entries, partner a nearest neighbour
+  uint32_t *trans;      // kMoveN x 2 words: move entries (see kMoveN)
 };
 
-// Move entries are indexed by pair state pc = 4 code_a + code_b and the pair's
-// choice byte mod 12 (12 is a multiple of both q-set sizes, 4 and 6).
-constexpr int kTransN = 16 * 12;
+// Move entries: one uint2 per (r, near, pc), entry (2 r + near) * 16 + pc, i.e.
+// at byte offset 256 r + 128 near + 8 pc -- r the pair's choice field mod 12
+// (12 is a multiple of both q-set sizes, 4 and 6), near whether the partner is a
+// nearest neighbour, pc = 4 code_a + code_b the pair state.
+constexpr int kTransN = 16 * 12;     // entries of one kind (far or near)
+constexpr int kMoveN = 2 * kTransN;  // both kinds
 constexpr int kThrHiWords = (kTableN + 1) / 2 * 2;  // padded to an even count
 
 struct LaunchCfg {
@@ -66,8 +68,7 @@ struct JobDesc {
   Geo g;                    // the lattice in global memory
   const uint32_t *thrhi;    // its tables
   const uint32_t *thr32;
-  const uint32_t *trans_far;
-  const uint32_t *trans_near;
+  const uint32_t *trans;
   int64_t nsweeps;          // sweeps to run in this launch
   int64_t *ring;            // observable ring (records every obs_every sweeps)
   int64_t ring_cap;
@@ -82,18 +83,17 @@ struct MultiJob {
   Geo g;
   const uint32_t *thrhi;
   const uint32_t *thr32;
-  const uint32_t *trans_far;
-  const uint32_t *trans_near;
+  const uint32_t *trans;
   int cta_begin, cta_count;
 };
 
 // Shared memory of the resident kernel besides the lattice words.
-constexpr int kResTableWords = kThrHiWords + 4 * kTransN;
+constexpr int kResTableWords = kThrHiWords + 2 * kMoveN;
 
 // Host-side table builders (ccmc_tables.cpp).
 void build_thresholds(double beta, double Delta, double V, double J, uint32_t *thr32);
 // Returns false if some entry could index outside the threshold table.
-bool build_transitions(uint32_t *trans_far, uint32_t *trans_near);
+bool build_transitions(uint32_t *trans);
 
 // Launchers (ccmc_kernels.cu).
 cudaError_t launch_init(const Geo &g, int h, int64_t n_plus, int64_t n_minus, cudaStream_t s);

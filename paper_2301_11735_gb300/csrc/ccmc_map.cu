@@ -6,8 +6,7 @@
 // change with atomic XORs of their own bits.
 //
 // The move uses the library's own tables: the 64-bit move entry of the pair's
-// state and choice (trans_near when b is a nearest neighbour of a, trans_far
-// otherwise), the dp4a threshold index from (sum_a (S+1) - sum_b (S+1) + 8,
+// state, choice and kind (partner a nearest neighbour of a or not), the dp4a threshold index from (sum_a (S+1) - sum_b (S+1) + 8,
 // sum_a (sigma+1), sum_b (sigma+1)) and the full 32-bit threshold.  Random
 // words of pair p of map m: R = word 0 of Philox(seed, (p, m_lo, m_hi, 11))
 // (bits 0-15 the choice v, bits 16-31 the acceptance word's top half) and,
@@ -50,8 +49,7 @@ __device__ __forceinline__ uint32_t g_plus1(uint32_t c) { return (0x1102u >> (4 
 __global__ void __launch_bounds__(256) map_kernel(Geo g, const int32_t *__restrict__ pairs,
                                                   int64_t npairs, uint32_t m_lo, uint32_t m_hi,
                                                   const uint32_t *__restrict__ thr32,
-                                                  const uint2 *__restrict__ trans_far,
-                                                  const uint2 *__restrict__ trans_near) {
+                                                  const uint2 *__restrict__ trans) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= npairs) return;
   const int a = pairs[2 * p], b = pairs[2 * p + 1];
@@ -97,8 +95,8 @@ __global__ void __launch_bounds__(256) map_kernel(Geo g, const int32_t *__restri
     r = sl.y % 12u;
   }
   const uint32_t pc = (ca << 2) | cb;
-  const uint2 e = (near ? trans_near : trans_far)[pc * 12u + r];
-  const uint32_t x = e.y >> 24;  // pc XOR the chosen configuration
+  const uint2 e = trans[(2u * r + (near ? 1u : 0u)) * 16u + pc];
+  const uint32_t x = e.y >> 28;  // pc XOR the chosen configuration
   if (x == 0u) return;           // the chosen configuration is the current one
   const uint32_t env = (SA + 8u - SB) | (GA << 8) | (GB << 16);
   const uint32_t thr = thr32[__dp4a((int)e.y, (int)env, (int)e.x)];
@@ -124,7 +122,7 @@ cudaError_t launch_map(const Geo &g, const int32_t *d_pairs, int64_t npairs, uin
   const int64_t blocks = (npairs + 255) / 256;
   map_kernel<<<(unsigned)blocks, 256, 0, s>>>(
       g, d_pairs, npairs, (uint32_t)m, (uint32_t)(m >> 32), t.thr32,
-      reinterpret_cast<const uint2 *>(t.trans_far), reinterpret_cast<const uint2 *>(t.trans_near));
+      reinterpret_cast<const uint2 *>(t.trans));
   return cudaGetLastError();
 }
 

@@ -22,15 +22,15 @@ namespace ccmc {
 //
 // Per pair, with pc = 4 code_a + code_b and its 32-bit random word R (16-bit
 // choice v in the low half, top half u of the acceptance word in the high):
-//   entry  = trans[pc][v mod 12]  -> base, byte coefficients, pc XOR npc
+//   entry  = trans[v mod 12][near][pc]  -> base, byte coefficients, pc XOR npc
 //   index  = dp4a(coefficients, (D8, GA, GB, 0), base)  (threshold index)
 //   accept = R < thrhi[index], i.e. u < the threshold's top half (v < 2^16)
 // The fast decision is always applied.  A tie of the top halves, or a choice
-// field v >= 65532, marks the pair rare: the exact path then undoes the fast
-// decision and applies the exact one with the pair's SLOW random words
-// (about one pair in 10^4).
+// field v >= 65532, makes the word rare: the exact path then re-examines its
+// pairs and, for each truly rare one, undoes the fast decision and applies the
+// exact one with the pair's SLOW random words (about one pair in 10^4).
 struct PhaseSmem {
-  uint2 trans[kTransN];
+  uint2 trans[kMoveN];
   uint32_t thrhi[kThrHiWords];
   Sched sched;
 };
@@ -102,13 +102,100 @@ __device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, co
   }
 }
 
+// Move entry of choice class r (v mod 12) and pc8 = 8 pc + 128 near: byte
+// offset 256 r + pc8 of the move table.
+__device__ __forceinline__ uint2 move_entry(const uint2 *trans, uint32_t r, uint32_t pc8) {
+  return *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(trans) + r * 256u + pc8);
+}
+
+// v mod 12 for v < 2^16: v - 12 floor(v / 12), the quotient by a multiply-high
+// (floor(v m / 2^32) with m = ceil(2^32 / 12) is exact for v < 2^16).
+__device__ __forceinline__ uint32_t mod12(uint32_t v) {
+  return v - 12u * __umulhi(v, 357913942u);
+}
+
+// Byte lanes of a word's groups (see phase_word): x01/x23 hold (D8, GA) of
+// pairs 0, 1 / 2, 3 of group k, gb the GB of its four pairs.
+struct GroupEnv {
+  uint32_t x01[4], x23[4], gb[4];
+};
+
+// dp4a operand (D8, GA, GB, 0) of pair t = 4 b + k (t, b, k compile-time
+// constants in the main loop).
+__device__ __forceinline__ uint32_t pair_env(const GroupEnv &ge, int b, int k) {
+  return b == 0 ? prmt(ge.x01[k], ge.gb[k], 0x8410u)
+       : b == 1 ? prmt(ge.x01[k], ge.gb[k], 0x8532u)
+       : b == 2 ? prmt(ge.x23[k], ge.gb[k], 0x8610u)
+                : prmt(ge.x23[k], ge.gb[k], 0x8732u);
+}
+
+// The exact path of a word (see phase_word): for each pair of the flagged
+// groups (bit t of slow) whose fast decision is not certain, undo it and apply
+// the exact one; returns the corrected (dA, dB).
+template <bool kAligned>
+__device__ __forceinline__ uint2 exact_path(const uint2 *trans, const uint32_t *thrhi,
+                                            const uint32_t *thr32, uint32_t k0, uint32_t k1,
+                                            uint32_t gbase, uint32_t slow0, int n, uint64_t P,
+                                            uint32_t near128, uint32_t A, uint32_t B, Sums sa,
+                                            Sums sb, uint32_t slow, uint32_t dA, uint32_t dB) {
+  U4 mv{0u, 0u, 0u, 0u};
+  int mv_group = -1;
+  while (slow) {
+    const int t = __ffs(slow) - 1;
+    slow &= slow - 1u;
+    if (!kAligned && t >= n) continue;
+    if ((t >> 2) != mv_group) {
+      mv_group = t >> 2;
+      mv = philox(gbase + (uint32_t)mv_group, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, k0, k1);
+    }
+    const int qw = t & 3;
+    const uint32_t R = qw == 0 ? mv.x : qw == 1 ? mv.y : qw == 2 ? mv.z : mv.w;
+    const uint32_t pc = (((A >> (2 * t)) & 3u) << 2) | ((B >> (2 * t)) & 3u);
+    const uint32_t pc8 = pc * 8u + near128;
+    const uint32_t v = R & 0xFFFFu, uh = R >> 16;
+    const int sh = 4 * (t >> 1);
+    const uint32_t sa4 = (((t & 1) ? sa.so : sa.se) >> sh) & 15u;
+    const uint32_t sb4 = (((t & 1) ? sb.so : sb.se) >> sh) & 15u;
+    const uint32_t ga4 = (((t & 1) ? sa.go : sa.ge) >> sh) & 15u;
+    const uint32_t gb4 = (((t & 1) ? sb.go : sb.ge) >> sh) & 15u;
+    const uint32_t env = (sa4 + 8u - sb4) | (ga4 << 8) | (gb4 << 16);
+    // the fast path's decision for this pair
+    const uint2 ef = move_entry(trans, mod12(v), pc8);
+    const uint32_t THf = thrhi[__dp4a((int)ef.y, (int)env, (int)ef.x)];
+    if (R - THf >= 0x10000u && v < 65532u) continue;  // not rare: the fast decision stands
+    if (R < THf) {  // undo it
+      const uint32_t x = ef.y >> 28;
+      dA ^= (x >> 2) << (2 * t);
+      dB ^= (x & 3u) << (2 * t);
+    }
+    const U4 sl = philox(slow0 + (uint32_t)t, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, k0, k1);
+    uint32_t rc;
+    if (v < 65532u)
+      rc = mod12(v);
+    else if (sl.y < 4294967292u)
+      rc = sl.y % 12u;
+    else
+      continue;  // keep the current configuration
+    const uint2 e = move_entry(trans, rc, pc8);
+    const uint32_t thr = thr32[__dp4a((int)e.y, (int)env, (int)e.x)];
+    const uint32_t uu = (uh << 16) | (sl.x & 0xFFFFu);
+    if (thr == 0xFFFFFFFFu || uu < thr) {
+      const uint32_t x = e.y >> 28;
+      dA ^= (x >> 2) << (2 * t);
+      dB ^= (x & 3u) << (2 * t);
+    }
+  }
+  return make_uint2(dA, dB);
+}
+
 // j: the pair's row in the class (keys the random streams); jr: the row of the
 // a word in u's arrays (j itself for the lattice in global memory, the row
-// inside a staged tile otherwise).
+// inside a staged tile otherwise); near128: 128 if the phase's partners are
+// nearest neighbours, else 0.
 template <int kMode>
 __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
                                            const uint32_t *thrhi, const uint32_t *thr32, int j,
-                                           int jr, int w, uint64_t P) {
+                                           int jr, int w, uint64_t P, uint32_t near128) {
   constexpr bool kAligned = kMode != kRowGeneral;
   // row jr + dy of a class (periodic in Cy); staged bands start at the right row
   auto row = [&](int r0, int dy) { return kMode == kRowTile ? r0 : wrap(r0 + dy, g.Cy); };
@@ -118,124 +205,98 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
   // ---- gather: the a word, the b window and the eight neighbour windows
   uint32_t *rowA = const_cast<uint32_t *>(u.cA) + jr * g.W;
   const uint32_t A = rowA[w];
-  Sums sa{0u, 0u, 0u, 0u}, sb{0u, 0u, 0u, 0u};
-  add_neighbour(sa, window<kMode>(u.cAL, g, u, jr, w, u.offAL, n));
-  add_neighbour(sa, window<kMode>(u.cAR, g, u, jr, w, u.offAR, n));
-  add_neighbour(sa, u.cAU[row(jr, u.dyAU) * g.W + w]);
-  add_neighbour(sa, u.cAD[row(jr, u.dyAD) * g.W + w]);
   const int jb = row(jr, u.qy);
   const uint32_t B = window<kMode>(u.cB, g, u, jb, w, u.offB, n);
-  add_neighbour(sb, window<kMode>(u.cBL, g, u, jb, w, u.offBL, n));
-  add_neighbour(sb, window<kMode>(u.cBR, g, u, jb, w, u.offBR, n));
-  add_neighbour(sb, window<kMode>(u.cBU, g, u, row(jb, u.dyBU), w, u.offB, n));
-  add_neighbour(sb, window<kMode>(u.cBD, g, u, row(jb, u.dyBD), w, u.offB, n));
+  const Sums sa = neighbour_sums(window<kMode>(u.cAL, g, u, jr, w, u.offAL, n),
+                                 window<kMode>(u.cAR, g, u, jr, w, u.offAR, n),
+                                 u.cAU[row(jr, u.dyAU) * g.W + w], u.cAD[row(jr, u.dyAD) * g.W + w]);
+  const Sums sb = neighbour_sums(window<kMode>(u.cBL, g, u, jb, w, u.offBL, n),
+                                 window<kMode>(u.cBR, g, u, jb, w, u.offBR, n),
+                                 window<kMode>(u.cBU, g, u, row(jb, u.dyBU), w, u.offB, n),
+                                 window<kMode>(u.cBD, g, u, row(jb, u.dyBD), w, u.offB, n));
 
   // ---- pair states in 4-bit lanes: lane u of pcE is site 2u, of pcO site 2u+1
   const uint32_t pcE = ((A & 0x33333333u) << 2) | (B & 0x33333333u);
   const uint32_t pcO = (A & 0xCCCCCCCCu) | ((B >> 2) & 0x33333333u);
 
-  // ---- byte lanes of group k (sites k, k+4, k+8, k+12): D8 = SA - SB + 8, GA, GB
-  uint32_t x01[4], x23[4], gbk[4];
+  // ---- byte lanes of group k (sites k, k+4, k+8, k+12): D8 = SA - SB + 8, GA,
+  // GB, and the move-table offsets 8 pc + near128 of the group's pairs
+  GroupEnv ge;
+  uint32_t pck[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const uint32_t d8 = group_bytes(sa.se, sa.so, k) + 0x08080808u - group_bytes(sb.se, sb.so, k);
     const uint32_t ga = group_bytes(sa.ge, sa.go, k);
-    gbk[k] = group_bytes(sb.ge, sb.go, k);
-    x01[k] = prmt(d8, ga, 0x5140u);
-    x23[k] = prmt(d8, ga, 0x7362u);
+    ge.gb[k] = group_bytes(sb.ge, sb.go, k);
+    ge.x01[k] = prmt(d8, ga, 0x5140u);
+    ge.x23[k] = prmt(d8, ga, 0x7362u);
+    pck[k] = group_bytes(pcE, pcO, k) * 8u + near128 * 0x01010101u;
   }
 
   // ---- random words: pair (i, j) of the class takes word i mod 4 of
-  // Philox(seed, (j Cx4 + i / 4, P_lo, P_hi, MOVE)); call b covers pairs 4b..4b+3
+  // Philox(seed, (j Cx4 + i / 4, P_lo, P_hi, MOVE)); call b covers pairs 4b..4b+3.
+  // Accepted moves (pc XOR npc, bits 28-31 of the entry) are shifted into accE
+  // (even pairs) and accO (odd pairs): pair 2m ends in lane m of accE.
   const uint32_t gbase = (uint32_t)j * (uint32_t)g.Cx4 + (uint32_t)(4 * w);
-  uint32_t dE = 0u, dO = 0u, slow = 0u;
+  uint32_t accE = 0u, accO = 0u;
+  uint32_t slow = 0u;  // bit t: pair t's group needs the exact path
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     if (!kAligned && 4 * b >= n) break;
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;  // smallest R - TH, largest v of the group
     const U4 r = philox(gbase + (uint32_t)b, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0,
                         g.k1);
-    uint32_t mn = 0xFFFFFFFFu, mx = 0u;  // smallest R ^ TH and largest v of the group
+    uint32_t d0 = 0xFFFFFFFFu, v0 = 0u;  // pair k - 1's (k odd)
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int t = 4 * b + k;
-      if (!kAligned && t >= n) continue;
+      if (!kAligned && t >= n) {  // past the end of the row: no pair
+        if (k & 1) {
+          mn = min(mn, d0);
+          mx = max(mx, v0);
+        }
+        continue;
+      }
       const uint32_t R = k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w;
-      const uint32_t env = b == 0 ? prmt(x01[k], gbk[k], 0x8410u)
-                         : b == 1 ? prmt(x01[k], gbk[k], 0x8532u)
-                         : b == 2 ? prmt(x23[k], gbk[k], 0x8610u)
-                                  : prmt(x23[k], gbk[k], 0x8732u);
-      const uint32_t pc = (((t & 1) ? pcO : pcE) >> (4 * (t >> 1))) & 15u;
+      const uint32_t env = pair_env(ge, b, k);
+      const uint32_t pc8 = prmt(pck[k], 0u, 0x4440u + (uint32_t)b);
       const uint32_t v = R & 0xFFFFu;
-      const uint32_t r12 = v - 12u * ((v * 43691u) >> 19);  // v mod 12 for v < 2^16
-      const uint2 e = trans[pc * 12u + r12];
-      const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
-      const uint32_t TH = thrhi[idx];
-      mn = min(mn, R ^ TH);
-      mx = max(mx, v);
-      // move bits of this pair (e.y bits 24-27) added at its 4-bit lane
-      const uint32_t xm = (e.y >> 24) * (1u << (4 * (t >> 1)));
+      const uint2 e = move_entry(trans, mod12(v), pc8);
+      const uint32_t TH = thrhi[__dp4a((int)e.y, (int)env, (int)e.x)];
+      const uint32_t d = R - TH;  // < 2^16 iff the top halves tie (TH's low half is 0)
+      if (k & 1) {
+        mn = __vimin3_u32(mn, d0, d);
+        mx = __vimax3_u32(mx, v0, v);
+      } else {
+        d0 = d;
+        v0 = v;
+      }
+      const uint32_t xm = R < TH ? (e.y & 0xF0000000u) : 0u;
       if (t & 1)
-        dO += R < TH ? xm : 0u;
+        accO = (accO >> 4) | xm;
       else
-        dE += R < TH ? xm : 0u;
+        accE = (accE >> 4) | xm;
     }
-    // a tie of the top halves (R ^ TH < 2^16) or a choice field >= 65532 makes
-    // the group's pairs go through the exact path
+    // a tie of the top halves (R - TH < 2^16) or a choice field v >= 65532
+    // sends the group's pairs through the exact path
     if (mn < 0x10000u || mx >= 65532u) slow |= 0xFu << (4 * b);
   }
-  uint32_t dA = ((dE >> 2) & 0x33333333u) | (((dO >> 2) & 0x33333333u) << 2);
-  uint32_t dB = (dE & 0x33333333u) | ((dO & 0x33333333u) << 2);
+  if constexpr (!kAligned) {
+    // lanes of missing pairs were never shifted in: align pair 0 to lane 0
+    const int ne = (n + 1) >> 1, no = n >> 1;
+    if (ne < 8) accE = ne == 0 ? 0u : accE >> (4 * (8 - ne));
+    if (no < 8) accO = no == 0 ? 0u : accO >> (4 * (8 - no));
+  }
+  uint32_t dA = ((accE >> 2) & 0x33333333u) | (((accO >> 2) & 0x33333333u) << 2);
+  uint32_t dB = (accE & 0x33333333u) | ((accO & 0x33333333u) << 2);
 
-  // ---- exact path for the flagged groups: for each truly rare pair, undo the
-  // fast decision and apply the exact one
-  U4 mv{0u, 0u, 0u, 0u};
-  int mv_group = -1;
-  while (slow) {
-    const int t = __ffs(slow) - 1;
-    slow &= slow - 1u;
-    if (!kAligned && t >= n) continue;
-    if ((t >> 2) != mv_group) {
-      mv_group = t >> 2;
-      mv = philox(gbase + (uint32_t)mv_group, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0,
-                  g.k1);
-    }
-    const int qw = t & 3;
-    const uint32_t R = qw == 0 ? mv.x : qw == 1 ? mv.y : qw == 2 ? mv.z : mv.w;
-    const uint32_t pc = (((A >> (2 * t)) & 3u) << 2) | ((B >> (2 * t)) & 3u);
-    const uint32_t v = R & 0xFFFFu, uh = R >> 16;
-    const int sh = 4 * (t >> 1);
-    const uint32_t sa4 = (((t & 1) ? sa.so : sa.se) >> sh) & 15u;
-    const uint32_t sb4 = (((t & 1) ? sb.so : sb.se) >> sh) & 15u;
-    const uint32_t ga4 = (((t & 1) ? sa.go : sa.ge) >> sh) & 15u;
-    const uint32_t gb4 = (((t & 1) ? sb.go : sb.ge) >> sh) & 15u;
-    const uint32_t env = (sa4 + 8u - sb4) | (ga4 << 8) | (gb4 << 16);
-    // the fast path's decision for this pair
-    const uint2 ef = trans[pc * 12u + v % 12u];
-    const uint32_t THf = thrhi[__dp4a((int)ef.y, (int)env, (int)ef.x)];
-    if ((R ^ THf) >= 0x10000u && v < 65532u) continue;  // not rare: the fast decision stands
-    if (R < THf) {  // undo it
-      const uint32_t x = ef.y >> 24;
-      dA ^= (x >> 2) << (2 * t);
-      dB ^= (x & 3u) << (2 * t);
-    }
-    const uint64_t kk = (uint64_t)j * g.Cx + s0 + t;
-    const U4 sl = philox((uint32_t)kk, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, g.k0, g.k1);
-    uint32_t r;
-    if (v < 65532u)
-      r = v % 12u;
-    else if (sl.y < 4294967292u)
-      r = sl.y % 12u;
-    else
-      continue;  // keep the current configuration
-    const uint2 e = trans[pc * 12u + r];
-    const int idx = __dp4a((int)e.y, (int)env, (int)e.x);
-    const uint32_t thr = thr32[idx];
-    const uint32_t uu = (uh << 16) | (sl.x & 0xFFFFu);
-    if (thr == 0xFFFFFFFFu || uu < thr) {
-      const uint32_t x = e.y >> 24;
-      dA ^= (x >> 2) << (2 * t);
-      dB ^= (x & 3u) << (2 * t);
-    }
+  // ---- exact path for the flagged groups (about one group in 10^4)
+  if (slow) {
+    const uint2 d = exact_path<kAligned>(trans, thrhi, thr32, g.k0, g.k1, gbase,
+                                         (uint32_t)((uint64_t)j * g.Cx + s0), n, P, near128, A,
+                                         B, sa, sb, slow, dA, dB);
+    dA = d.x;
+    dB = d.y;
   }
   if constexpr (!kAligned) {
     if (n < 16) {
@@ -273,9 +334,8 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
 
 template <bool kAligned>
 __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *thrhi,
-                                                    const uint32_t *thr32,
-                                                    const uint32_t *trans_far,
-                                                    const uint32_t *trans_near, int64_t p_off) {
+                                                    const uint32_t *thr32, const uint32_t *trans,
+                                                    int64_t p_off) {
   __shared__ PhaseSmem sm;
   // The tables come from host uploads that precede the whole launch chain, so
   // they are loaded before waiting for the previous kernel of the stream (which
@@ -293,18 +353,19 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *th
   }
   __syncthreads();
   const Sched sc = sm.sched;
-  const uint32_t *trans = sc.near ? trans_near : trans_far;
-  for (int t = threadIdx.x; t < kTransN; t += blockDim.x)
+  for (int t = threadIdx.x; t < kMoveN; t += blockDim.x)
     sm.trans[t] = make_uint2(trans[2 * t], trans[2 * t + 1]);
   __syncthreads();
   const PhaseU u = phase_uniform(g, sc);
+  const uint32_t near128 = sc.near ? 128u : 0u;
   const int nw = g.Cy * g.W;
   int wid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
   int j = wid / g.W, w = wid - j * g.W;
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
-    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, thr32, j, j, w, P);
+    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, thr32, j, j, w, P,
+                                                      near128);
     w += sw;
     j += sj;
     if (w >= g.W) {
@@ -317,8 +378,10 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *th
 // ----------------------------------------------------------------------------
 // Tile-staged phase (lattices whose class rows are W words with W dividing 256
 // and a multiple of 4, and Cy a multiple of R = 256 / W).  A tile is R
-// consecutive rows of the a-class (256 words, one per thread).  Thread 0 stages
-// a tile's ten row bands -- the a rows, the b rows and the rows of all eight
+// consecutive rows of the a-class (256 words, one per thread); CTA c takes
+// tiles c, c + grid, c + 2 grid, ...  (Handing out tiles by an atomic counter
+// measured slower: the claim's latency lands on the staging thread.)  Thread 0
+// stages a tile's ten row bands -- the a rows, the b rows and the rows of all eight
 // neighbour classes, each band R full rows -- into shared memory with bulk
 // asynchronous copies that complete on the buffer's `full` mbarrier; the
 // threads evaluate their words from shared memory; each warp then arrives on
@@ -339,14 +402,14 @@ constexpr int kTileBufs = 3;
 constexpr int kTileWarps = kTileWords / 32;
 constexpr int kWaitSpins = 1 << 20;  // bounded mbarrier waits
 
-// The lattice's threshold tops and both move tables, contiguous in device
-// memory (thrhi, trans_far, trans_near), staged with one bulk copy.
-constexpr uint32_t kStagedTableBytes = 4u * (kThrHiWords + 4 * kTransN);
+// The lattice's threshold tops and the move table, contiguous in device
+// memory (thrhi, trans), staged with one bulk copy.
+constexpr uint32_t kStagedTableBytes = 4u * (kThrHiWords + 2 * kMoveN);
 static_assert(kStagedTableBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 
 struct TileSmem {
   alignas(128) uint32_t thrhi[kThrHiWords];
-  uint2 trans[2][kTransN];  // far, near: directly after thrhi, as in device memory
+  uint2 trans[kMoveN];  // directly after thrhi, as in device memory
   alignas(128) uint32_t band[kTileBufs][kBands][kTileWords];
   alignas(8) unsigned long long full[kTileBufs];  // bands landed (transaction count)
   alignas(8) unsigned long long done[kTileBufs];  // every warp finished the tile
@@ -404,8 +467,6 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 
 __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_t *thrhi,
                                                             const uint32_t *thr32,
-                                                            const uint32_t *trans_far,
-                                                            const uint32_t *trans_near,
                                                             int64_t p_off) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
   TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem);
@@ -436,7 +497,7 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
   }
   __syncthreads();
   const Sched sc = sm.sched;
-  const uint2 *trans = sm.trans[sc.near ? 1 : 0];
+  const uint32_t near128 = sc.near ? 128u : 0u;
   const PhaseU u = phase_uniform(g, sc);
   const int W = g.W, R = kTileWords / W, Cy = g.Cy;
   const Band bands[kBands] = {{u.cA, 0},          {u.cAL, 0},          {u.cAR, 0},
@@ -535,7 +596,7 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
       lu.cBR = base + 7 * kTileWords;
       lu.cBU = base + 8 * kTileWords;
       lu.cBD = base + 9 * kTileWords;
-      phase_word<kRowTile>(g, lu, trans, sm.thrhi, thr32, tile * R + jr, jr, w, P);
+      phase_word<kRowTile>(g, lu, sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P, near128);
     } else {
       sm.err = 1;
     }
@@ -594,11 +655,11 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
   }
   __syncthreads();
   const Sched sc = sm.sched;
-  const uint32_t *trans = sc.near ? J.trans_near : J.trans_far;
-  for (int t = threadIdx.x; t < kTransN; t += blockDim.x)
-    sm.trans[t] = make_uint2(trans[2 * t], trans[2 * t + 1]);
+  for (int t = threadIdx.x; t < kMoveN; t += blockDim.x)
+    sm.trans[t] = make_uint2(J.trans[2 * t], J.trans[2 * t + 1]);
   __syncthreads();
   const PhaseU u = phase_uniform(g, sc);
+  const uint32_t near128 = sc.near ? 128u : 0u;
   const int nw = g.Cy * g.W;
   int wid = ((int)blockIdx.x - J.cta_begin) * blockDim.x + threadIdx.x;
   const int stride = J.cta_count * blockDim.x;
@@ -606,7 +667,7 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
     phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, J.thr32, j, j, w,
-                                                      P);
+                                                      P, near128);
     w += sw;
     j += sj;
     if (w >= g.W) {
@@ -628,8 +689,7 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
                                                        int *queue) {
   extern __shared__ __align__(16) uint32_t dyn[];
   uint32_t *s_thrhi = dyn;
-  uint2 *s_far = reinterpret_cast<uint2 *>(dyn + kThrHiWords);
-  uint2 *s_near = s_far + kTransN;
+  uint2 *s_trans = reinterpret_cast<uint2 *>(dyn + kThrHiWords);
   uint32_t *s_words = dyn + kResTableWords;
   __shared__ Sched s_sched[8];  // the schedules of the current sweep's phases
   __shared__ int s_job;
@@ -644,10 +704,8 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
     const Geo g = J.g;
     const int64_t nw = 16 * g.cstride;
     for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) s_thrhi[t] = J.thrhi[t];
-    for (int t = threadIdx.x; t < kTransN; t += blockDim.x) {
-      s_far[t] = make_uint2(J.trans_far[2 * t], J.trans_far[2 * t + 1]);
-      s_near[t] = make_uint2(J.trans_near[2 * t], J.trans_near[2 * t + 1]);
-    }
+    for (int t = threadIdx.x; t < kMoveN; t += blockDim.x)
+      s_trans[t] = make_uint2(J.trans[2 * t], J.trans[2 * t + 1]);
     for (int64_t t = threadIdx.x; t < nw; t += blockDim.x) s_words[t] = g.words[t];
     const int64_t P0 = g.ctl[kCtlPhaseBase];
     const int64_t nsweeps = J.nsweeps;
@@ -671,13 +729,13 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
         const uint64_t P = (uint64_t)(P0 + 8 * s + p);
         const Sched sc = s_sched[p];
         const PhaseU u = phase_uniform(gs, sc);
-        const uint2 *tr = sc.near ? s_near : s_far;
+        const uint32_t near128 = sc.near ? 128u : 0u;
         for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
           const int j = wid / g.W, w = wid - j * g.W;
           if (aligned)
-            phase_word<kRowAligned>(gs, u, tr, s_thrhi, J.thr32, j, j, w, P);
+            phase_word<kRowAligned>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128);
           else
-            phase_word<kRowGeneral>(gs, u, tr, s_thrhi, J.thr32, j, j, w, P);
+            phase_word<kRowGeneral>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128);
         }
         __syncthreads();
       }
@@ -775,17 +833,16 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
   if (cfg.tile_grid > 0) {
     const int64_t tiles = nw / kTileWords;
     const int grid = (int)(tiles < cfg.tile_grid ? tiles : cfg.tile_grid);
-    if (t.trans_far != t.thrhi + kThrHiWords || t.trans_near != t.trans_far + 2 * kTransN ||
-        (reinterpret_cast<uintptr_t>(t.thrhi) & 15u))
+    if (t.trans != t.thrhi + kThrHiWords || (reinterpret_cast<uintptr_t>(t.thrhi) & 15u))
       return cudaErrorInvalidValue;  // the tables must be one staged block
     return launch_pdl_smem(phase_tile_kernel, grid, 256, sizeof(TileSmem), s, g, t.thrhi,
-                           t.thr32, t.trans_far, t.trans_near, p_off);
+                           t.thr32, p_off);
   }
   const int grid = grid_for(nw, 256, cfg.phase_grid_cap);
-  const uint32_t *thrhi = t.thrhi, *thr32 = t.thr32, *tf = t.trans_far, *tn = t.trans_near;
+  const uint32_t *thrhi = t.thrhi, *thr32 = t.thr32, *tr = t.trans;
   if ((g.Cx & 15) == 0)
-    return launch_pdl(phase_kernel<true>, grid, 256, s, g, thrhi, thr32, tf, tn, p_off);
-  return launch_pdl(phase_kernel<false>, grid, 256, s, g, thrhi, thr32, tf, tn, p_off);
+    return launch_pdl(phase_kernel<true>, grid, 256, s, g, thrhi, thr32, tr, p_off);
+  return launch_pdl(phase_kernel<false>, grid, 256, s, g, thrhi, thr32, tr, p_off);
 }
 
 cudaError_t launch_phase_multi(const MultiJob *d_jobs, int njobs, int grid, bool aligned,

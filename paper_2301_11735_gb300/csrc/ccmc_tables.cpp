@@ -39,20 +39,22 @@ void build_thresholds(double beta, double Delta, double V, double J, uint32_t *t
             threshold(beta, Delta, V, J, 2 * dqi - 2, dBV, dBJ);
 }
 
-// Move entries (see the phase kernel).  For pair state pc = 4 a + b and choice
-// class r = v mod 12, the proposed state is the (r mod |set|)-th configuration
-// of the pair's q-set in the paper's order (Sec. 3.1); frozen pairs (|q| = 2)
-// propose themselves.  dE of the move:
+// Move entries (see the phase kernel).  For choice class r = v mod 12, kind
+// near (the partner is a nearest neighbour) and pair state pc = 4 a + b, the
+// proposed state is the (r mod |set|)-th configuration of the pair's q-set in
+// the paper's order (Sec. 3.1); frozen pairs (|q| = 2) propose themselves.  dE
+// of the move:
 //   dBV = dS_a sum_<a> S + dS_b sum_<b> S + m dS_a dS_b
 //   dBJ = dsig_a sum_<a> sigma + dsig_b sum_<b> sigma + m dsig_a dsig_b
-// with neighbour sums over old states (partner included) and m the number of
-// a-b bonds.  As dS_b = -dS_a, the threshold index
+// with neighbour sums over old states (partner included) and m = near the number
+// of a-b bonds.  As dS_b = -dS_a, the threshold index
 //   ((dQ + 2)/2 * 41 + dBV + 20) * 41 + dBJ + 20
 // is an affine function of the biased sums D8 = sum_<a> S - sum_<b> S + 8,
 // GA = sum_<a> sigma + 4, GB = sum_<b> sigma + 4:
 //   index = base + (41 dS_a) D8 + dsig_a GA + dsig_b GB.
-// Entry word 0 holds base; word 1 holds the signed byte coefficients
-// (41 dS_a, dsig_a, dsig_b) and, in its top byte, pc XOR npc.
+// Entry (2 r + near) * 16 + pc: word 0 holds base; word 1 the signed byte
+// coefficients (41 dS_a, dsig_a, dsig_b) and, in its top four bits, pc XOR npc
+// (the phase kernel multiplies byte 3 by zero).
 namespace {
 constexpr int kSetN[3] = {4, 6, 4};  // q = +1, 0, -1
 constexpr int kSets[3][6][2] = {
@@ -62,7 +64,7 @@ constexpr int kSets[3][6][2] = {
 };
 }  // namespace
 
-bool build_transitions(uint32_t *trans_far, uint32_t *trans_near) {
+bool build_transitions(uint32_t *trans) {
   int lo = 1 << 30, hi = -(1 << 30);
   for (int pc = 0; pc < 16; ++pc) {
     const int ca = pc >> 2, cb = pc & 3;
@@ -82,12 +84,12 @@ bool build_transitions(uint32_t *trans_far, uint32_t *trans_near) {
       const int near_base = base + kNB * dSa * dSb + dGa * dGb;
       const uint32_t x = (uint32_t)(((ca ^ na) << 2) | (cb ^ nb));
       const uint32_t coef = ((uint32_t)mulS & 0xFFu) | (((uint32_t)dGa & 0xFFu) << 8) |
-                            (((uint32_t)dGb & 0xFFu) << 16) | (x << 24);
-      const int e = pc * 12 + r;
-      trans_far[2 * e] = (uint32_t)base;
-      trans_far[2 * e + 1] = coef;
-      trans_near[2 * e] = (uint32_t)near_base;
-      trans_near[2 * e + 1] = coef;
+                            (((uint32_t)dGb & 0xFFu) << 16) | (x << 28);
+      for (int near = 0; near < 2; ++near) {
+        const int e = (2 * r + near) * 16 + pc;
+        trans[2 * e] = (uint32_t)(near ? near_base : base);
+        trans[2 * e + 1] = coef;
+      }
       // every index an entry can form, over all possible neighbour sums
       // (D8 in [0, 16], GA and GB in [0, 8]), must stay inside the table
       for (int b0 : {base, near_base})
