@@ -416,6 +416,7 @@ struct TileSmem {
   alignas(8) unsigned long long tables;           // the tables landed
   Sched sched;
   int err;
+  int busy0, busy1;  // classes the previous phase writes (early staging waits for them)
   unsigned staged;  // thread 0: buffers whose bulk loads it has not waited for
   unsigned dpar;    // thread 0, bit b: parity of the phase of done[b] waited for next
 };
@@ -488,12 +489,29 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
                  : "memory");
     bulk_load(smem_u32(sm.thrhi), thrhi, kStagedTableBytes, bar);
   }
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;");
+  // The phase index.  A launch after the first of a chain (p_off > 0) reads the
+  // counter base before it waits for its predecessor: the base was written by
+  // a kernel at least two launches back (the chain's counter advance), which
+  // the predecessor's griddepcontrol.wait has already waited for.  It then
+  // stages the bands of its first tile that lie in classes the predecessor
+  // (phase P - 1, whose schedule it draws too) does not write, while that
+  // phase is still finishing, and the other bands once it has finished.
+  const bool early = p_off > 0;
+  if (!early) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+  }
   const uint64_t P = (uint64_t)(g.ctl[kCtlPhaseBase] + p_off);
   if (threadIdx.x < 32) {
     const Sched sc = draw_schedule(g, P);
     if (threadIdx.x == 0) sm.sched = sc;
+    if (early) {
+      const Sched pv = draw_schedule(g, P - 1u);
+      if (threadIdx.x == 0) {
+        sm.busy0 = pv.a0y * 4 + pv.a0x;
+        sm.busy1 = ((pv.a0y + pv.ry) & 3) * 4 + ((pv.a0x + pv.rx) & 3);
+      }
+    }
   }
   __syncthreads();
   const Sched sc = sm.sched;
@@ -506,30 +524,39 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
                               {u.cBD, u.qy + u.dyBD}};
   const int ntiles = Cy / R;
   const uint32_t row_bytes = (uint32_t)W * 4u;
+  // row r (in [-Cy, 2 Cy)) of a class, periodic
+  auto wrap_row = [&](int r) { return r < 0 ? r + Cy : (r >= Cy ? r - Cy : r); };
 
-  // thread 0 stages tile `tile` into buffer `buf`
-  auto stage = [&](int tile, int buf) {
+  // thread 0: the bands of tile `tile` selected by `mask` into buffer `buf`
+  auto stage_bands = [&](int tile, int buf, unsigned mask) {
     const uint32_t bar = smem_u32(&sm.full[buf]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"((uint32_t)(kBands * kTileWords * 4))
-                 : "memory");
     const int j0 = tile * R;
     for (int k = 0; k < kBands; ++k) {
-      int r0 = (j0 + bands[k].dy) % Cy;
-      if (r0 < 0) r0 += Cy;
+      if (!(mask & (1u << k))) continue;
+      const int r0 = wrap_row(wrap_row(j0 + bands[k].dy));
       const int n1 = min(R, Cy - r0);
       const uint32_t dst = smem_u32(&sm.band[buf][k][0]);
       bulk_load(dst, bands[k].cls + (int64_t)r0 * W, (uint32_t)n1 * row_bytes, bar);
       if (n1 < R) bulk_load(dst + (uint32_t)n1 * row_bytes, bands[k].cls, (uint32_t)(R - n1) * row_bytes, bar);
     }
   };
+  auto expect_tile = [&](int buf) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     smem_u32(&sm.full[buf])),
+                 "r"((uint32_t)(kBands * kTileWords * 4))
+                 : "memory");
+  };
+  // thread 0 stages tile `tile` into buffer `buf`
+  auto stage = [&](int tile, int buf) {
+    expect_tile(buf);
+    stage_bands(tile, buf, (1u << kBands) - 1u);
+  };
   // thread 0 sends the a and b bands of tile `tile` (buffer `buf`) back
   auto write_back = [&](int tile, int buf) {
     const int j0 = tile * R;
     bulk_store(const_cast<uint32_t *>(u.cA) + (int64_t)j0 * W, smem_u32(&sm.band[buf][0][0]),
                (uint32_t)R * row_bytes);
-    int rb = (j0 + u.qy) % Cy;
-    if (rb < 0) rb += Cy;
+    const int rb = wrap_row(j0 + u.qy);
     const int n1 = min(R, Cy - rb);
     const uint32_t src = smem_u32(&sm.band[buf][5][0]);
     bulk_store(const_cast<uint32_t *>(u.cB) + (int64_t)rb * W, src, (uint32_t)n1 * row_bytes);
@@ -539,13 +566,25 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
   };
 
-  if (threadIdx.x == 0) {
-    sm.staged = 0u;
-    sm.dpar = 0u;
-    if (blockIdx.x < (unsigned)ntiles) {
-      stage(blockIdx.x, 0);
-      sm.staged = 1u;
+  if (early) {
+    unsigned busy = 0u;  // bands in the classes the previous phase writes
+    for (int k = 0; k < kBands; ++k)
+      if (bands[k].cls == g.words + (int64_t)sm.busy0 * g.cstride ||
+          bands[k].cls == g.words + (int64_t)sm.busy1 * g.cstride)
+        busy |= 1u << k;
+    if (threadIdx.x == 0 && blockIdx.x < (unsigned)ntiles) {
+      expect_tile(0);
+      stage_bands(blockIdx.x, 0, ~busy & ((1u << kBands) - 1u));
     }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (threadIdx.x == 0 && blockIdx.x < (unsigned)ntiles) stage_bands(blockIdx.x, 0, busy);
+  } else if (threadIdx.x == 0 && blockIdx.x < (unsigned)ntiles) {
+    stage(blockIdx.x, 0);
+  }
+  if (threadIdx.x == 0) {
+    sm.staged = blockIdx.x < (unsigned)ntiles ? 1u : 0u;
+    sm.dpar = 0u;
   }
   __syncthreads();  // the mbarrier initialisation
   if (!mbar_wait(smem_u32(&sm.tables), 0u)) sm.err = 1;
