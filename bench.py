@@ -42,7 +42,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-STEP_SWEEPS = 10
+# Sweeps of every lattice per timed step (long enough for the nvidia-smi clock
+# samples, taken every 50 ms, to fall inside the timed region).
+STEP_SWEEPS = {"temperature4096": 200, "large16384": 50}
+OBS_EVERY = {"temperature4096": 10, "large16384": 1}
 
 # Counters of one phase launch of the bench's dominant kernel, from the ncu
 # captures summarised in profiles/phase_tile_kernel_<workload>.md:
@@ -214,18 +217,21 @@ def max_over_ranks(x: float, dist, device) -> float:
     return float(t.item())
 
 
-def workload(name: str):
-    """(sims, description) of a named bench workload."""
+def workload(name: str, step_sweeps: int = 0):
+    """(sims, description) of a named bench workload; step_sweeps: sweeps of
+    every lattice per step (0: the workload's default)."""
     from workloads import large_16384, temperature_sweep_4096
 
     if name == "large16384":
-        return [large_16384(obs_every=1)], (
-            "16384x16384 near the charge-ordering crossover (Delta=0.2, V=1, J=0.5, n=0.05, "
-            "T=0.6), 10 sweeps per step, observables and histograms of M, M_stag, S_stag every "
-            "sweep")
-    return temperature_sweep_4096(obs_every=STEP_SWEEPS), (
-        "4096x4096 temperature sweep: 4 lattices (T=0.2,0.5,1,2; Delta=0, V=0.5, J=1, n=0.1, "
-        "c=0.3), 10 sweeps each per step")
+        return [large_16384(obs_every=OBS_EVERY[name])], (
+            f"16384x16384 near the charge-ordering crossover (Delta=0.2, V=1, J=0.5, n=0.05, "
+            f"T=0.6), {step_sweeps or STEP_SWEEPS[name]} sweeps per step, observables and "
+            f"histograms of M, M_stag, S_stag every sweep")
+    name = "temperature4096"
+    return temperature_sweep_4096(obs_every=OBS_EVERY[name]), (
+        f"4096x4096 temperature sweep: 4 lattices (T=0.2,0.5,1,2; Delta=0, V=0.5, J=1, n=0.1, "
+        f"c=0.3), {step_sweeps or STEP_SWEEPS[name]} sweeps each per step, observables every "
+        f"{OBS_EVERY[name]} sweeps")
 
 
 def run_reference(args):
@@ -450,8 +456,12 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    sims, workload_desc = workload(args.workload)
+    sims, workload_desc = workload(args.workload, args.sweeps_per_step)
     sims = rank_sims(sims, rank)
+    step_sweeps = args.sweeps_per_step or STEP_SWEEPS[args.workload]
+    if step_sweeps % sims[0].obs_every:
+        raise SystemExit(f"--sweeps-per-step must be a multiple of {sims[0].obs_every}")
+    recs_per_step = step_sweeps // sims[0].obs_every
     # explicit streams: one issuing stream for the timing events and the L2 flush,
     # one per lattice so that the four run concurrently (torch's default stream
     # has handle 0, which the library reads as "create your own")
@@ -473,7 +483,7 @@ def run_ours(args):
         ev0.record(main)
         for st in streams:
             st.wait_event(ev0)
-        batch.sweep(STEP_SWEEPS, *cols, obs_every=sims[0].obs_every)
+        batch.sweep(step_sweeps, *cols, obs_every=sims[0].obs_every)
         for st in streams:
             e = torch.cuda.Event()
             e.record(st)
@@ -505,7 +515,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_s = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
     clocks = sampler.summary()
-    updates_per_step = sum(s.sites for s in sims) * STEP_SWEEPS
+    updates_per_step = sum(s.sites for s in sims) * step_sweeps
     value = updates_per_step * args.steps * world / total_s
 
     # dominant kernel: the colour phase of one 4096^2 lattice.  A chunk of 16
@@ -555,8 +565,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for lat, s, h in zip(lats, sims, host_states):
             lat.set_state_packed_ptr(h.data_ptr(), s.seed, 0)
-        batch.sweep(STEP_SWEEPS, *cols, obs_every=sims[0].obs_every)
-        recs = [lat.obs_series(cap=16) for lat in lats]
+        batch.sweep(step_sweeps, *cols, obs_every=sims[0].obs_every)
+        recs = [lat.obs_series(cap=recs_per_step) for lat in lats]
         dt = time.perf_counter() - t0
         rec_bytes = sum(r.nbytes for r in recs)
         if k > 0:
@@ -571,12 +581,12 @@ def run_ours(args):
             "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": workload_desc,
-                       "lattices_per_gpu": len(sims), "sweeps_per_step": STEP_SWEEPS,
+                       "lattices_per_gpu": len(sims), "sweeps_per_step": step_sweeps,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
             "clocks": clocks, "wall_s": t_wall,
-            # per step and lattice: 80 phase launches, the recounts, counter advances
+            # per step and lattice: 8 phase launches a sweep, the recounts, counter advances
             "gpu_launches": args.steps * len(sims) * launches_per_call(
-                STEP_SWEEPS, sims[0].obs_every, STEP_SWEEPS),
+                step_sweeps, sims[0].obs_every, step_sweeps),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": counters["traffic"] if counters else None,
@@ -611,6 +621,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-side", action="store_true",
                     help="skip the batched-replica and served-stream measurements")
+    ap.add_argument("--sweeps-per-step", type=int, default=0,
+                    help="sweeps of every lattice per step (default: the workload's)")
     ap.add_argument("--workload", default="temperature4096",
                     choices=["temperature4096", "large16384"],
                     help="temperature4096 (default): four 4096^2 lattices; large16384: one "

@@ -108,6 +108,12 @@ int tile_resident_grid();
 // One colour phase of every lattice in d_jobs (all aligned or all not).
 cudaError_t launch_phase_multi(const MultiJob *d_jobs, int njobs, int grid, bool aligned,
                                int64_t p_off, cudaStream_t s);
+// One tile-staged phase of every lattice in d_jobs (all take the tile path;
+// their tables one staged block each, as launch_phase requires).
+cudaError_t launch_phase_tile_multi(const MultiJob *d_jobs, int njobs, int grid, int64_t p_off,
+                                    cudaStream_t s);
+// Tiles of one tile-staged phase of lattice g.
+int tile_count(const Geo &g);
 cudaError_t launch_recount(const Geo &g, int64_t *partials, int64_t *ring, int64_t ring_cap,
                            int64_t *hist, int nbins, int64_t sweep_off, cudaStream_t s);
 cudaError_t launch_advance(int64_t *ctl, int64_t phases, cudaStream_t s);

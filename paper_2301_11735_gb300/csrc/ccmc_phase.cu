@@ -466,9 +466,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_t *thrhi,
-                                                            const uint32_t *thr32,
-                                                            int64_t p_off) {
+// One tile-staged phase of lattice g by CTA `cta` of the `ncta` CTAs that
+// work on it.
+__device__ __forceinline__ void tile_phase(const Geo &g, const uint32_t *thrhi,
+                                           const uint32_t *thr32, int64_t p_off, int cta,
+                                           int ncta) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
   TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem);
   static_assert(offsetof(TileSmem, trans) == 4 * kThrHiWords, "tables staged as one block");
@@ -495,8 +497,10 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
   // the predecessor's griddepcontrol.wait has already waited for.  It then
   // stages the bands of its first tile that lie in classes the predecessor
   // (phase P - 1, whose schedule it draws too) does not write, while that
-  // phase is still finishing, and the other bands once it has finished.
-  const bool early = p_off > 0;
+  // phase is still finishing, and the other bands once it has finished.  Only
+  // lattices whose phases give every CTA several tiles do this: for smaller ones
+  // it measured slower when several lattices share the GPU on their own streams.
+  const bool early = p_off > 0 && g.Cy / (kTileWords / g.W) > ncta;
   if (!early) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
@@ -572,18 +576,18 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
       if (bands[k].cls == g.words + (int64_t)sm.busy0 * g.cstride ||
           bands[k].cls == g.words + (int64_t)sm.busy1 * g.cstride)
         busy |= 1u << k;
-    if (threadIdx.x == 0 && blockIdx.x < (unsigned)ntiles) {
+    if (threadIdx.x == 0 && cta < ntiles) {
       expect_tile(0);
-      stage_bands(blockIdx.x, 0, ~busy & ((1u << kBands) - 1u));
+      stage_bands(cta, 0, ~busy & ((1u << kBands) - 1u));
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    if (threadIdx.x == 0 && blockIdx.x < (unsigned)ntiles) stage_bands(blockIdx.x, 0, busy);
-  } else if (threadIdx.x == 0 && blockIdx.x < (unsigned)ntiles) {
-    stage(blockIdx.x, 0);
+    if (threadIdx.x == 0 && cta < ntiles) stage_bands(cta, 0, busy);
+  } else if (threadIdx.x == 0 && cta < ntiles) {
+    stage(cta, 0);
   }
   if (threadIdx.x == 0) {
-    sm.staged = blockIdx.x < (unsigned)ntiles ? 1u : 0u;
+    sm.staged = cta < ntiles ? 1u : 0u;
     sm.dpar = 0u;
   }
   __syncthreads();  // the mbarrier initialisation
@@ -594,13 +598,13 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
   const bool lane0 = (threadIdx.x & 31) == 0;
   uint32_t fpar = 0u;  // bit b: parity of the phase of full[b] waited for next
   int buf = 0, k = 0;
-  int tile = blockIdx.x;
-  for (; tile < ntiles; tile += gridDim.x, ++k) {
+  int tile = cta;
+  for (; tile < ntiles; tile += ncta, ++k) {
     if (threadIdx.x == 0) {
       // (1) stage the next tile into the buffer of tile k - 2, whose
       // write-back (issued one tile ago, the only copies outstanding) must
       // have finished reading it
-      const int next = tile + gridDim.x;
+      const int next = tile + ncta;
       if (next < ntiles) {
         const int nb = buf == kTileBufs - 1 ? 0 : buf + 1;
         asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
         const int pb = buf == 0 ? kTileBufs - 1 : buf - 1;
         if (mbar_wait(smem_u32(&sm.done[pb]), (sm.dpar >> pb) & 1u)) {
           sm.dpar ^= 1u << pb;
-          write_back(tile - gridDim.x, pb);
+          write_back(tile - ncta, pb);
         } else {
           sm.err = 1;
         }
@@ -653,7 +657,7 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
       // the last tile
       const int pb = buf == 0 ? kTileBufs - 1 : buf - 1;
       if (mbar_wait(smem_u32(&sm.done[pb]), (sm.dpar >> pb) & 1u))
-        write_back(tile - gridDim.x, pb);
+        write_back(tile - ncta, pb);
       else
         sm.err = 1;
     }
@@ -666,6 +670,24 @@ __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_
       g.ctl[kCtlStatus] = 1;
     }
   }
+}
+
+__global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_t *thrhi,
+                                                            const uint32_t *thr32,
+                                                            int64_t p_off) {
+  tile_phase(g, thrhi, thr32, p_off, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Lock-step tile-staged phase of several lattices in one launch: CTAs
+// [cta_begin, cta_begin + cta_count) of the grid work on job j, each lattice
+// with its own tables, phase counter and schedule.
+__global__ void __launch_bounds__(256, 4) phase_tile_multi_kernel(const MultiJob *__restrict__ jobs,
+                                                                  int njobs, int64_t p_off) {
+  int j = 0;
+  while (j + 1 < njobs && (int)blockIdx.x >= jobs[j + 1].cta_begin) ++j;
+  const MultiJob &J = jobs[j];
+  const Geo g = J.g;
+  tile_phase(g, J.thrhi, J.thr32, p_off, (int)blockIdx.x - J.cta_begin, J.cta_count);
 }
 
 // Lock-step phase of several lattices in one launch: each CTA works on one
@@ -843,6 +865,8 @@ int phase_resident_grid(bool aligned) {
   return per_sm * sms;
 }
 
+int tile_count(const Geo &g) { return g.Cy / (kTileWords / g.W); }
+
 bool tile_path_ok(const Geo &g) {
   return (g.Cx & 15) == 0 && (g.W & 3) == 0 && g.W <= kTileWords && kTileWords % g.W == 0 &&
          g.Cy % (kTileWords / g.W) == 0;
@@ -856,6 +880,8 @@ int tile_resident_grid() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (cudaFuncSetAttribute(phase_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(TileSmem)) != cudaSuccess ||
+      cudaFuncSetAttribute(phase_tile_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(TileSmem)) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel, 256,
                                                     sizeof(TileSmem)) != cudaSuccess ||
@@ -882,6 +908,12 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
   if ((g.Cx & 15) == 0)
     return launch_pdl(phase_kernel<true>, grid, 256, s, g, thrhi, thr32, tr, p_off);
   return launch_pdl(phase_kernel<false>, grid, 256, s, g, thrhi, thr32, tr, p_off);
+}
+
+cudaError_t launch_phase_tile_multi(const MultiJob *d_jobs, int njobs, int grid, int64_t p_off,
+                                    cudaStream_t s) {
+  return launch_pdl_smem(phase_tile_multi_kernel, grid, 256, sizeof(TileSmem), s, d_jobs, njobs,
+                         p_off);
 }
 
 cudaError_t launch_phase_multi(const MultiJob *d_jobs, int njobs, int grid, bool aligned,

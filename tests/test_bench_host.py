@@ -27,3 +27,12 @@ def test_workloads():
     assert len(sims) == 4 and all(s.Lx == 4096 for s in sims) and "4096" in desc
     sims, desc = bench.workload("large16384")
     assert len(sims) == 1 and sims[0].Lx == 16384 and sims[0].obs_every == 1
+
+
+def test_step_lengths():
+    # every timed step ends on an observable record, and is long enough for
+    # several 50 ms clock samples (about 15 ms a step on a GB300)
+    for name, sweeps in bench.STEP_SWEEPS.items():
+        assert sweeps % bench.OBS_EVERY[name] == 0
+        sims, _ = bench.workload(name)
+        assert sum(s.sites for s in sims) * sweeps >= 10 ** 10

@@ -155,11 +155,14 @@ def test_autotuner_picks_a_valid_shape_and_results_stay_exact(cc, tmp_path, monk
 
 
 @pytest.mark.parametrize("shapes", [[(512, 512)] * 8 + [(256, 256)],
-                                    [(516, 260)] * 8 + [(1024, 1024)]])
+                                    [(516, 260)] * 8 + [(1024, 1024)],
+                                    [(1024, 1024)] * 4 + [(512, 512)] * 2 + [(1024, 512)] * 2])
 def test_large_lattices_in_lockstep_equal_individual_runs(cc, shapes):
-    """Eight or more large lattices at the same sweep advance with one phase
-    launch for all of them (a lock-step group); each must still match its own
-    run.  A small resident limit sends every lattice down the large path."""
+    """Eight or more lattices at the same sweep advance with one phase launch
+    for all of them (a lock-step group: the tile-staged kernel in the first and
+    third cases, with uneven tile counts in the third; the direct kernel for the
+    eight 516 x 260); each must still match its own run.  A small resident limit
+    sends every lattice down the large path."""
     n = len(shapes)
     seeds = [20 + i for i in range(n)]
     Ts = [0.2 + 0.25 * i for i in range(n)]
