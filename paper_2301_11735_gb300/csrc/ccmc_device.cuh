@@ -27,6 +27,15 @@ struct U4 {
   uint32_t x, y, z, w;
 };
 
+// The 64-bit product of two 32-bit words as its low and high halves (one wide
+// multiply instead of a low and a high one).
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi) {
+  uint64_t p;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+  lo = (uint32_t)p;
+  hi = (uint32_t)(p >> 32);
+}
+
 __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                      uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -42,6 +51,54 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
   }
   return U4{c0, c1, c2, c3};
 }
+
+// The round keys of a seed, precomputed: round r uses (k0 + r 0x9E3779B9,
+// k1 + r 0xBB67AE85).  Passed as a kernel parameter, each key is a constant
+// operand of its round's XOR instead of an addition per call.
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+
+inline RoundKeys round_keys(uint32_t k0, uint32_t k1) {
+  RoundKeys rk;
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
+    rk.k1[r] = k1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     const RoundKeys &rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0, hi0, lo1, hi1;
+    mul_wide(0xD2511F53u, c0, lo0, hi0);
+    mul_wide(0xCD9E8D57u, c2, lo1, hi1);
+    c0 = hi1 ^ c1 ^ rk.k0[r];
+    c2 = hi0 ^ c3 ^ rk.k1[r];
+    c1 = lo1;
+    c3 = lo0;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// Where a kernel's Philox keys come from: the seed (keys added per round) or
+// precomputed round keys.
+struct SeedKeys {
+  uint32_t k0, k1;
+  __device__ __forceinline__ U4 operator()(uint32_t c0, uint32_t c1, uint32_t c2,
+                                           uint32_t c3) const {
+    return philox(c0, c1, c2, c3, k0, k1);
+  }
+};
+struct TableKeys {
+  const RoundKeys *rk;
+  __device__ __forceinline__ U4 operator()(uint32_t c0, uint32_t c1, uint32_t c2,
+                                           uint32_t c3) const {
+    return philox(c0, c1, c2, c3, *rk);
+  }
+};
 
 __device__ __forceinline__ uint32_t *row_ptr(const Geo &g, int cls, int row) {
   return g.words + (int64_t)cls * g.cstride + (int64_t)row * g.W;

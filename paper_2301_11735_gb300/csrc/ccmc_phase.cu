@@ -191,11 +191,13 @@ __device__ __forceinline__ uint2 exact_path(const uint2 *trans, const uint32_t *
 // j: the pair's row in the class (keys the random streams); jr: the row of the
 // a word in u's arrays (j itself for the lattice in global memory, the row
 // inside a staged tile otherwise); near128: 128 if the phase's partners are
-// nearest neighbours, else 0.
-template <int kMode>
+// nearest neighbours, else 0; keys: the source of the Philox keys (SeedKeys or
+// TableKeys of the lattice's seed).
+template <int kMode, class Keys = SeedKeys>
 __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
                                            const uint32_t *thrhi, const uint32_t *thr32, int j,
-                                           int jr, int w, uint64_t P, uint32_t near128) {
+                                           int jr, int w, uint64_t P, uint32_t near128,
+                                           const Keys &keys) {
   constexpr bool kAligned = kMode != kRowGeneral;
   // row jr + dy of a class (periodic in Cy); staged bands start at the right row
   auto row = [&](int r0, int dy) { return kMode == kRowTile ? r0 : wrap(r0 + dy, g.Cy); };
@@ -244,8 +246,7 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
   for (int b = 0; b < 4; ++b) {
     if (!kAligned && 4 * b >= n) break;
     uint32_t mn = 0xFFFFFFFFu, mx = 0u;  // smallest R - TH, largest v of the group
-    const U4 r = philox(gbase + (uint32_t)b, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0,
-                        g.k1);
+    const U4 r = keys(gbase + (uint32_t)b, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE);
     uint32_t d0 = 0xFFFFFFFFu, v0 = 0u;  // pair k - 1's (k odd)
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *th
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
     phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, thr32, j, j, w, P,
-                                                      near128);
+                                                      near128, SeedKeys{g.k0, g.k1});
     w += sw;
     j += sj;
     if (w >= g.W) {
@@ -467,10 +468,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 }
 
 // One tile-staged phase of lattice g by CTA `cta` of the `ncta` CTAs that
-// work on it.
+// work on it; keys: the source of its Philox keys.
+template <class Keys>
 __device__ __forceinline__ void tile_phase(const Geo &g, const uint32_t *thrhi,
                                            const uint32_t *thr32, int64_t p_off, int cta,
-                                           int ncta) {
+                                           int ncta, const Keys &keys) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
   TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem);
   static_assert(offsetof(TileSmem, trans) == 4 * kThrHiWords, "tables staged as one block");
@@ -639,7 +641,8 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint32_t *thrhi,
       lu.cBR = base + 7 * kTileWords;
       lu.cBU = base + 8 * kTileWords;
       lu.cBD = base + 9 * kTileWords;
-      phase_word<kRowTile>(g, lu, sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P, near128);
+      phase_word<kRowTile>(g, lu, sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P, near128,
+                           keys);
     } else {
       sm.err = 1;
     }
@@ -673,9 +676,9 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint32_t *thrhi,
 }
 
 __global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_t *thrhi,
-                                                            const uint32_t *thr32,
-                                                            int64_t p_off) {
-  tile_phase(g, thrhi, thr32, p_off, (int)blockIdx.x, (int)gridDim.x);
+                                                            const uint32_t *thr32, int64_t p_off,
+                                                            const __grid_constant__ RoundKeys rk) {
+  tile_phase(g, thrhi, thr32, p_off, (int)blockIdx.x, (int)gridDim.x, TableKeys{&rk});
 }
 
 // Lock-step tile-staged phase of several lattices in one launch: CTAs
@@ -687,7 +690,8 @@ __global__ void __launch_bounds__(256, 4) phase_tile_multi_kernel(const MultiJob
   while (j + 1 < njobs && (int)blockIdx.x >= jobs[j + 1].cta_begin) ++j;
   const MultiJob &J = jobs[j];
   const Geo g = J.g;
-  tile_phase(g, J.thrhi, J.thr32, p_off, (int)blockIdx.x - J.cta_begin, J.cta_count);
+  tile_phase(g, J.thrhi, J.thr32, p_off, (int)blockIdx.x - J.cta_begin, J.cta_count,
+             SeedKeys{g.k0, g.k1});
 }
 
 // Lock-step phase of several lattices in one launch: each CTA works on one
@@ -728,7 +732,7 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
     phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, J.thr32, j, j, w,
-                                                      P, near128);
+                                                      P, near128, SeedKeys{g.k0, g.k1});
     w += sw;
     j += sj;
     if (w >= g.W) {
@@ -794,9 +798,11 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
         for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
           const int j = wid / g.W, w = wid - j * g.W;
           if (aligned)
-            phase_word<kRowAligned>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128);
+            phase_word<kRowAligned>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128,
+                                    SeedKeys{gs.k0, gs.k1});
           else
-            phase_word<kRowGeneral>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128);
+            phase_word<kRowGeneral>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128,
+                                    SeedKeys{gs.k0, gs.k1});
         }
         __syncthreads();
       }
@@ -901,7 +907,7 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
     if (t.trans != t.thrhi + kThrHiWords || (reinterpret_cast<uintptr_t>(t.thrhi) & 15u))
       return cudaErrorInvalidValue;  // the tables must be one staged block
     return launch_pdl_smem(phase_tile_kernel, grid, 256, sizeof(TileSmem), s, g, t.thrhi,
-                           t.thr32, p_off);
+                           t.thr32, p_off, round_keys(g.k0, g.k1));
   }
   const int grid = grid_for(nw, 256, cfg.phase_grid_cap);
   const uint32_t *thrhi = t.thrhi, *thr32 = t.thr32, *tr = t.trans;
