@@ -102,9 +102,13 @@ int upload_params_on(ccmc_lattice *h, double beta, double Delta, double V, doubl
     return CCMC_OK;
   std::vector<uint32_t> thr32(kTableN);
   std::vector<uint32_t> thrhi(kThrHiWords, 0);
+  std::vector<uint16_t> thrhi16(kThrHi16, 0);
   build_thresholds(beta, Delta, V, J, thr32.data());
   for (int i = 0; i < kTableN; ++i) thrhi[i] = thr32[i] & 0xFFFF0000u;
+  for (int i = 0; i < kTableN; ++i) thrhi16[i] = (uint16_t)(thr32[i] >> 16);
   CK(cudaMemcpyAsync(h->t.thr32, thr32.data(), sizeof(uint32_t) * kTableN,
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->t.thrhi16, thrhi16.data(), sizeof(uint16_t) * kThrHi16,
                      cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h->t.thrhi, thrhi.data(), sizeof(uint32_t) * kThrHiWords,
                      cudaMemcpyHostToDevice, st));
@@ -265,7 +269,10 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   const uint64_t N = (uint64_t)Lx * (uint64_t)Ly;
   g.rej = (0 - N) % N;
   h->cfg.phase_grid_cap = phase_resident_grid((g.Cx & 15) == 0);
-  if (tile_path_ok(g) && !std::getenv("CCMC_NO_TILE")) h->cfg.tile_grid = tile_resident_grid();
+  if (tile_path_ok(g) && !std::getenv("CCMC_NO_TILE")) {
+    h->cfg.tile_grid = tile_resident_grid();
+    h->cfg.tile_grid_small = tile_resident_grid_small();
+  }
   while (((int64_t)1 << (2 * h->h)) < (int64_t)N) ++h->h;
   h->ring_cap = obs_capacity > 0 ? obs_capacity : 4096;
   cudaGetDevice(&h->device);
@@ -287,7 +294,8 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
       cudaMalloc(&h->d_ring, sizeof(int64_t) * 8 * h->ring_cap) != cudaSuccess ||
       cudaMalloc(&h->d_flag, sizeof(int)) != cudaSuccess)
     return fail(CCMC_E_NOMEM);
-  const size_t tb = sizeof(uint32_t) * (kTableN + 2 * kMoveN + kThrHiWords);
+  const size_t tb = sizeof(uint32_t) * (kTableN + 4 * kMoveN + kThrHiWords) +
+                    sizeof(uint16_t) * kThrHi16;
   if (cudaMalloc(&h->d_tables, tb) != cudaSuccess) return fail(CCMC_E_NOMEM);
   // thrhi and the move table one after another (kStagedTableBytes, a
   // multiple of 16 from a 256-byte aligned base): the tile kernel copies them
@@ -297,12 +305,19 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   p += sizeof(uint32_t) * kThrHiWords;
   h->t.trans = (uint32_t *)p;
   p += sizeof(uint32_t) * 2 * kMoveN;
+  // the compact tile kernel's copy: 16-bit tops, then the move table again
+  h->t.thrhi16 = (uint16_t *)p;
+  p += sizeof(uint16_t) * kThrHi16;
+  h->t.trans16 = (uint32_t *)p;
+  p += sizeof(uint32_t) * 2 * kMoveN;
   h->t.thr32 = (uint32_t *)p;
   g.words = h->d_words;
   g.ctl = h->d_ctl;
   uint32_t tr[2 * kMoveN];
   if (!build_transitions(tr)) return fail(CCMC_E_INVAL);
   if (cudaMemcpyAsync(h->t.trans, tr, sizeof(tr), cudaMemcpyHostToDevice, h->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(h->t.trans16, tr, sizeof(tr), cudaMemcpyHostToDevice, h->stream) !=
           cudaSuccess ||
       cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t) * 16 * g.cstride, h->stream) !=
           cudaSuccess ||

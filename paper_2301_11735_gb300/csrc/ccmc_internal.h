@@ -48,6 +48,8 @@ struct DevTables {
   uint32_t *thrhi;      // kThrHiWords: each threshold with its low half cleared (fast path)
   uint32_t *thr32;      // kTableN: full thresholds (exact path)
   uint32_t *trans;      // kMoveN x 2 words: move entries (see kMoveN)
+  uint16_t *thrhi16;    // kThrHi16: each threshold's top 16 bits (compact fast path)
+  uint32_t *trans16;    // a copy of trans directly after thrhi16 (staged with it)
 };
 
 // Move entries: one uint2 per (r, near, pc), entry (2 r + near) * 16 + pc, i.e.
@@ -57,10 +59,12 @@ struct DevTables {
 constexpr int kTransN = 16 * 12;     // entries of one kind (far or near)
 constexpr int kMoveN = 2 * kTransN;  // both kinds
 constexpr int kThrHiWords = (kTableN + 1) / 2 * 2;  // padded to an even count
+constexpr int kThrHi16 = (kTableN + 7) / 8 * 8;     // 16-bit tops, padded to 16 bytes
 
 struct LaunchCfg {
   int phase_grid_cap = 152 * 3;  // one resident wave of phase_kernel (set at create)
   int tile_grid = 0;             // > 0: tile-staged phases, this many CTAs at most
+  int tile_grid_small = 0;       // one wave of the compact tile kernel (16-bit tops)
 };
 
 // One lattice of a resident batch launch (device array, filled on the host).
@@ -105,6 +109,8 @@ int phase_resident_grid(bool aligned);
 // Whether a lattice can take the tile-staged phase kernel, and its one wave.
 bool tile_path_ok(const Geo &g);
 int tile_resident_grid();
+// One wave of the compact tile kernel (more CTAs per SM), 0 if unavailable.
+int tile_resident_grid_small();
 // One colour phase of every lattice in d_jobs (all aligned or all not).
 cudaError_t launch_phase_multi(const MultiJob *d_jobs, int njobs, int grid, bool aligned,
                                int64_t p_off, cudaStream_t s);

@@ -114,6 +114,14 @@ __device__ __forceinline__ uint32_t mod12(uint32_t v) {
   return v - 12u * __umulhi(v, 357913942u);
 }
 
+// The top half of the threshold at idx, in the high 16 bits (the low 16 are
+// zero): from a table of 32-bit words with the low halves cleared, or of
+// 16-bit tops (half the shared memory, one shift more).
+__device__ __forceinline__ uint32_t thr_top(const uint32_t *thrhi, int idx) { return thrhi[idx]; }
+__device__ __forceinline__ uint32_t thr_top(const uint16_t *thrhi, int idx) {
+  return (uint32_t)thrhi[idx] << 16;
+}
+
 // Byte lanes of a word's groups (see phase_word): x01/x23 hold (D8, GA) of
 // pairs 0, 1 / 2, 3 of group k, gb the GB of its four pairs.
 struct GroupEnv {
@@ -132,8 +140,8 @@ __device__ __forceinline__ uint32_t pair_env(const GroupEnv &ge, int b, int k) {
 // The exact path of a word (see phase_word): for each pair of the flagged
 // groups (bit t of slow) whose fast decision is not certain, undo it and apply
 // the exact one; returns the corrected (dA, dB).
-template <bool kAligned>
-__device__ __forceinline__ uint2 exact_path(const uint2 *trans, const uint32_t *thrhi,
+template <bool kAligned, class ThrT>
+__device__ __forceinline__ uint2 exact_path(const uint2 *trans, const ThrT *thrhi,
                                             const uint32_t *thr32, uint32_t k0, uint32_t k1,
                                             uint32_t gbase, uint32_t slow0, int n, uint64_t P,
                                             uint32_t near128, uint32_t A, uint32_t B, Sums sa,
@@ -161,7 +169,7 @@ __device__ __forceinline__ uint2 exact_path(const uint2 *trans, const uint32_t *
     const uint32_t env = (sa4 + 8u - sb4) | (ga4 << 8) | (gb4 << 16);
     // the fast path's decision for this pair
     const uint2 ef = move_entry(trans, mod12(v), pc8);
-    const uint32_t THf = thrhi[__dp4a((int)ef.y, (int)env, (int)ef.x)];
+    const uint32_t THf = thr_top(thrhi, __dp4a((int)ef.y, (int)env, (int)ef.x));
     if (R - THf >= 0x10000u && v < 65532u) continue;  // not rare: the fast decision stands
     if (R < THf) {  // undo it
       const uint32_t x = ef.y >> 28;
@@ -193,9 +201,9 @@ __device__ __forceinline__ uint2 exact_path(const uint2 *trans, const uint32_t *
 // inside a staged tile otherwise); near128: 128 if the phase's partners are
 // nearest neighbours, else 0; keys: the source of the Philox keys (SeedKeys or
 // TableKeys of the lattice's seed).
-template <int kMode, class Keys = SeedKeys>
+template <int kMode, class Keys = SeedKeys, class ThrT = uint32_t>
 __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
-                                           const uint32_t *thrhi, const uint32_t *thr32, int j,
+                                           const ThrT *thrhi, const uint32_t *thr32, int j,
                                            int jr, int w, uint64_t P, uint32_t near128,
                                            const Keys &keys) {
   constexpr bool kAligned = kMode != kRowGeneral;
@@ -263,7 +271,7 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
       const uint32_t pc8 = prmt(pck[k], 0u, 0x4440u + (uint32_t)b);
       const uint32_t v = R & 0xFFFFu;
       const uint2 e = move_entry(trans, mod12(v), pc8);
-      const uint32_t TH = thrhi[__dp4a((int)e.y, (int)env, (int)e.x)];
+      const uint32_t TH = thr_top(thrhi, __dp4a((int)e.y, (int)env, (int)e.x));
       const uint32_t d = R - TH;  // < 2^16 iff the top halves tie (TH's low half is 0)
       if (k & 1) {
         mn = __vimin3_u32(mn, d0, d);
@@ -404,12 +412,19 @@ constexpr int kTileWarps = kTileWords / 32;
 constexpr int kWaitSpins = 1 << 20;  // bounded mbarrier waits
 
 // The lattice's threshold tops and the move table, contiguous in device
-// memory (thrhi, trans), staged with one bulk copy.
-constexpr uint32_t kStagedTableBytes = 4u * (kThrHiWords + 2 * kMoveN);
-static_assert(kStagedTableBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+// memory (thrhi, trans -- or the compact copy thrhi16, trans16), staged with
+// one bulk copy.  ThrT: uint32_t (tops in 32-bit words) or uint16_t (16-bit
+// tops: 10 KB less shared memory, so five CTAs fit an SM instead of four).
+template <class ThrT>
+struct TileTables {
+  static constexpr int kTops = sizeof(ThrT) == 4 ? kThrHiWords : kThrHi16;
+  static constexpr uint32_t kBytes = (uint32_t)sizeof(ThrT) * kTops + 8u * kMoveN;
+  static_assert(kBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+};
 
+template <class ThrT>
 struct TileSmem {
-  alignas(128) uint32_t thrhi[kThrHiWords];
+  alignas(128) ThrT thrhi[TileTables<ThrT>::kTops];
   uint2 trans[kMoveN];  // directly after thrhi, as in device memory
   alignas(128) uint32_t band[kTileBufs][kBands][kTileWords];
   alignas(8) unsigned long long full[kTileBufs];  // bands landed (transaction count)
@@ -469,13 +484,16 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 
 // One tile-staged phase of lattice g by CTA `cta` of the `ncta` CTAs that
 // work on it; keys: the source of its Philox keys.
-template <class Keys>
-__device__ __forceinline__ void tile_phase(const Geo &g, const uint32_t *thrhi,
+template <class ThrT, class Keys>
+__device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
                                            const uint32_t *thr32, int64_t p_off, int cta,
                                            int ncta, const Keys &keys) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
-  TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem);
-  static_assert(offsetof(TileSmem, trans) == 4 * kThrHiWords, "tables staged as one block");
+  using Smem = TileSmem<ThrT>;
+  constexpr uint32_t kStagedTableBytes = TileTables<ThrT>::kBytes;
+  Smem &sm = *reinterpret_cast<Smem *>(tile_smem);
+  static_assert(offsetof(Smem, trans) == sizeof(ThrT) * TileTables<ThrT>::kTops,
+                "tables staged as one block");
   if (threadIdx.x == 0) {
     sm.err = 0;
     for (int b = 0; b < kTileBufs; ++b) {
@@ -675,9 +693,14 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint32_t *thrhi,
   }
 }
 
-__global__ void __launch_bounds__(256, 4) phase_tile_kernel(Geo g, const uint32_t *thrhi,
-                                                            const uint32_t *thr32, int64_t p_off,
-                                                            const __grid_constant__ RoundKeys rk) {
+// ThrT, kMinBlocks: uint32_t tops at four CTAs per SM (the large-lattice
+// kernel: no register spills), or uint16_t tops at five (the compact kernel for
+// lattices whose phase fits one wave: more CTAs resident for several lattices
+// on their own streams, at 48 registers).
+template <class ThrT, int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) phase_tile_kernel(
+    Geo g, const ThrT *thrhi, const uint32_t *thr32, int64_t p_off,
+    const __grid_constant__ RoundKeys rk) {
   tile_phase(g, thrhi, thr32, p_off, (int)blockIdx.x, (int)gridDim.x, TableKeys{&rk});
 }
 
@@ -885,12 +908,29 @@ int tile_resident_grid() {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaFuncSetAttribute(phase_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(TileSmem)) != cudaSuccess ||
+  constexpr int bytes = (int)sizeof(TileSmem<uint32_t>);
+  if (cudaFuncSetAttribute(phase_tile_kernel<uint32_t, 4>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
       cudaFuncSetAttribute(phase_tile_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(TileSmem)) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel, 256,
-                                                    sizeof(TileSmem)) != cudaSuccess ||
+                           bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<uint32_t, 4>, 256,
+                                                    bytes) != cudaSuccess ||
+      per_sm < 1 || sms < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * sms;
+}
+
+int tile_resident_grid_small() {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  constexpr int bytes = (int)sizeof(TileSmem<uint16_t>);
+  if (cudaFuncSetAttribute(phase_tile_kernel<uint16_t, 5>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<uint16_t, 5>, 256,
+                                                    bytes) != cudaSuccess ||
       per_sm < 1 || sms < 1) {
     cudaGetLastError();
     return 0;
@@ -903,11 +943,21 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
   const int64_t nw = (int64_t)g.Cy * g.W;
   if (cfg.tile_grid > 0) {
     const int64_t tiles = nw / kTileWords;
+    if (t.trans != t.thrhi + kThrHiWords || (reinterpret_cast<uintptr_t>(t.thrhi) & 15u) ||
+        reinterpret_cast<const char *>(t.trans16) !=
+            reinterpret_cast<const char *>(t.thrhi16) + 2 * kThrHi16 ||
+        (reinterpret_cast<uintptr_t>(t.thrhi16) & 15u))
+      return cudaErrorInvalidValue;  // the tables must be staged blocks
+    // A phase that fits one wave of the compact kernel (one tile per CTA)
+    // takes it: measured faster for several such lattices on their own streams.
+    if (cfg.tile_grid_small > 0 && tiles <= cfg.tile_grid_small)
+      return launch_pdl_smem(phase_tile_kernel<uint16_t, 5>, (int)tiles, 256,
+                             sizeof(TileSmem<uint16_t>), s, g, (const uint16_t *)t.thrhi16,
+                             t.thr32, p_off, round_keys(g.k0, g.k1));
     const int grid = (int)(tiles < cfg.tile_grid ? tiles : cfg.tile_grid);
-    if (t.trans != t.thrhi + kThrHiWords || (reinterpret_cast<uintptr_t>(t.thrhi) & 15u))
-      return cudaErrorInvalidValue;  // the tables must be one staged block
-    return launch_pdl_smem(phase_tile_kernel, grid, 256, sizeof(TileSmem), s, g, t.thrhi,
-                           t.thr32, p_off, round_keys(g.k0, g.k1));
+    return launch_pdl_smem(phase_tile_kernel<uint32_t, 4>, grid, 256, sizeof(TileSmem<uint32_t>),
+                           s, g, (const uint32_t *)t.thrhi, t.thr32, p_off,
+                           round_keys(g.k0, g.k1));
   }
   const int grid = grid_for(nw, 256, cfg.phase_grid_cap);
   const uint32_t *thrhi = t.thrhi, *thr32 = t.thr32, *tr = t.trans;
@@ -918,8 +968,8 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
 
 cudaError_t launch_phase_tile_multi(const MultiJob *d_jobs, int njobs, int grid, int64_t p_off,
                                     cudaStream_t s) {
-  return launch_pdl_smem(phase_tile_multi_kernel, grid, 256, sizeof(TileSmem), s, d_jobs, njobs,
-                         p_off);
+  return launch_pdl_smem(phase_tile_multi_kernel, grid, 256, sizeof(TileSmem<uint32_t>), s,
+                         d_jobs, njobs, p_off);
 }
 
 cudaError_t launch_phase_multi(const MultiJob *d_jobs, int njobs, int grid, bool aligned,
