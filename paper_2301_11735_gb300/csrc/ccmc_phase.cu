@@ -422,13 +422,15 @@ struct TileTables {
   static_assert(kBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
 
-template <class ThrT>
+// kBufs: band buffers (three for the pipelined tile loop, one for a CTA that
+// takes a single tile).
+template <class ThrT, int kBufs = kTileBufs>
 struct TileSmem {
   alignas(128) ThrT thrhi[TileTables<ThrT>::kTops];
   uint2 trans[kMoveN];  // directly after thrhi, as in device memory
-  alignas(128) uint32_t band[kTileBufs][kBands][kTileWords];
-  alignas(8) unsigned long long full[kTileBufs];  // bands landed (transaction count)
-  alignas(8) unsigned long long done[kTileBufs];  // every warp finished the tile
+  alignas(128) uint32_t band[kBufs][kBands][kTileWords];
+  alignas(8) unsigned long long full[kBufs];  // bands landed (transaction count)
+  alignas(8) unsigned long long done[kBufs];  // every warp finished the tile
   alignas(8) unsigned long long tables;           // the tables landed
   Sched sched;
   int err;
@@ -484,19 +486,22 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 
 // One tile-staged phase of lattice g by CTA `cta` of the `ncta` CTAs that
 // work on it; keys: the source of its Philox keys.
-template <class ThrT, class Keys>
+// kSingle: every CTA takes exactly one tile (ncta == tiles): one band buffer,
+// no pipeline.
+template <class ThrT, bool kSingle, class Keys>
 __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
                                            const uint32_t *thr32, int64_t p_off, int cta,
                                            int ncta, const Keys &keys) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
-  using Smem = TileSmem<ThrT>;
+  constexpr int kBufs = kSingle ? 1 : kTileBufs;
+  using Smem = TileSmem<ThrT, kBufs>;
   constexpr uint32_t kStagedTableBytes = TileTables<ThrT>::kBytes;
   Smem &sm = *reinterpret_cast<Smem *>(tile_smem);
   static_assert(offsetof(Smem, trans) == sizeof(ThrT) * TileTables<ThrT>::kTops,
                 "tables staged as one block");
   if (threadIdx.x == 0) {
     sm.err = 0;
-    for (int b = 0; b < kTileBufs; ++b) {
+    for (int b = 0; b < kBufs; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.full[b])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.done[b])),
                    "r"(kTileWarps));
@@ -520,7 +525,7 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
   // phase is still finishing, and the other bands once it has finished.  Only
   // lattices whose phases give every CTA several tiles do this: for smaller ones
   // it measured slower when several lattices share the GPU on their own streams.
-  const bool early = p_off > 0 && g.Cy / (kTileWords / g.W) > ncta;
+  const bool early = !kSingle && p_off > 0 && g.Cy / (kTileWords / g.W) > ncta;
   if (!early) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
@@ -616,6 +621,53 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
   const int lw = __ffs(W) - 1;  // W is a power of two
   const int jr = threadIdx.x >> lw, w = threadIdx.x & (W - 1);
   const bool lane0 = (threadIdx.x & 31) == 0;
+  // a tile's bands from buffer buf as the windows' sources
+  auto local_u = [&](int buf) {
+    const uint32_t *base = sm.band[buf][0];
+    PhaseU lu = u;
+    lu.cA = base;
+    lu.cAL = base + 1 * kTileWords;
+    lu.cAR = base + 2 * kTileWords;
+    lu.cAU = base + 3 * kTileWords;
+    lu.cAD = base + 4 * kTileWords;
+    lu.cB = base + 5 * kTileWords;
+    lu.cBL = base + 6 * kTileWords;
+    lu.cBR = base + 7 * kTileWords;
+    lu.cBU = base + 8 * kTileWords;
+    lu.cBD = base + 9 * kTileWords;
+    return lu;
+  };
+  if constexpr (kSingle) {
+    // one tile: evaluate it, then thread 0 sends its a and b bands back
+    if (cta < ntiles) {
+      if (mbar_wait(smem_u32(&sm.full[0]), 0u)) {
+        if (threadIdx.x == 0) sm.staged = 0u;
+        phase_word<kRowTile>(g, local_u(0), sm.trans, sm.thrhi, thr32, cta * R + jr, jr, w, P,
+                             near128, keys);
+      } else {
+        sm.err = 1;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane0) mbar_arrive(smem_u32(&sm.done[0]));
+    if (threadIdx.x == 0) {
+      if (cta < ntiles && !sm.err) {
+        if (mbar_wait(smem_u32(&sm.done[0]), 0u))
+          write_back(cta, 0);
+        else
+          sm.err = 1;
+      }
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+      if (sm.err) {
+        // give loads still in flight a bounded chance to land before exiting
+        mbar_wait(smem_u32(&sm.tables), 0u);
+        if (sm.staged & 1u) mbar_wait(smem_u32(&sm.full[0]), 0u);
+        g.ctl[kCtlStatus] = 1;
+      }
+    }
+    return;
+  }
   uint32_t fpar = 0u;  // bit b: parity of the phase of full[b] waited for next
   int buf = 0, k = 0;
   int tile = cta;
@@ -647,20 +699,8 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
     fpar ^= 1u << buf;
     if (ok) {
       if (threadIdx.x == 0) sm.staged &= ~(1u << buf);
-      const uint32_t *base = sm.band[buf][0];
-      PhaseU lu = u;
-      lu.cA = base;
-      lu.cAL = base + 1 * kTileWords;
-      lu.cAR = base + 2 * kTileWords;
-      lu.cAU = base + 3 * kTileWords;
-      lu.cAD = base + 4 * kTileWords;
-      lu.cB = base + 5 * kTileWords;
-      lu.cBL = base + 6 * kTileWords;
-      lu.cBR = base + 7 * kTileWords;
-      lu.cBU = base + 8 * kTileWords;
-      lu.cBD = base + 9 * kTileWords;
-      phase_word<kRowTile>(g, lu, sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P, near128,
-                           keys);
+      phase_word<kRowTile>(g, local_u(buf), sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P,
+                           near128, keys);
     } else {
       sm.err = 1;
     }
@@ -693,15 +733,17 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
   }
 }
 
-// ThrT, kMinBlocks: uint32_t tops at four CTAs per SM (the large-lattice
-// kernel: no register spills), or uint16_t tops at five (the compact kernel for
-// lattices whose phase fits one wave: more CTAs resident for several lattices
-// on their own streams, at 48 registers).
-template <class ThrT, int kMinBlocks>
+// ThrT, kMinBlocks, kSingle: uint32_t tops at four CTAs per SM with the
+// pipelined tile loop (the large-lattice kernel: no register spills), or
+// uint16_t tops at five CTAs per SM, one tile per CTA and one band buffer (the
+// compact kernel for lattices whose phase fits one wave: more CTAs resident
+// for several lattices on their own streams, at 48 registers).
+template <class ThrT, int kMinBlocks, bool kSingle>
 __global__ void __launch_bounds__(256, kMinBlocks) phase_tile_kernel(
     Geo g, const ThrT *thrhi, const uint32_t *thr32, int64_t p_off,
     const __grid_constant__ RoundKeys rk) {
-  tile_phase(g, thrhi, thr32, p_off, (int)blockIdx.x, (int)gridDim.x, TableKeys{&rk});
+  tile_phase<ThrT, kSingle>(g, thrhi, thr32, p_off, (int)blockIdx.x, (int)gridDim.x,
+                            TableKeys{&rk});
 }
 
 // Lock-step tile-staged phase of several lattices in one launch: CTAs
@@ -713,8 +755,8 @@ __global__ void __launch_bounds__(256, 4) phase_tile_multi_kernel(const MultiJob
   while (j + 1 < njobs && (int)blockIdx.x >= jobs[j + 1].cta_begin) ++j;
   const MultiJob &J = jobs[j];
   const Geo g = J.g;
-  tile_phase(g, J.thrhi, J.thr32, p_off, (int)blockIdx.x - J.cta_begin, J.cta_count,
-             SeedKeys{g.k0, g.k1});
+  tile_phase<uint32_t, false>(g, J.thrhi, J.thr32, p_off, (int)blockIdx.x - J.cta_begin,
+                              J.cta_count, SeedKeys{g.k0, g.k1});
 }
 
 // Lock-step phase of several lattices in one launch: each CTA works on one
@@ -909,11 +951,11 @@ int tile_resident_grid() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   constexpr int bytes = (int)sizeof(TileSmem<uint32_t>);
-  if (cudaFuncSetAttribute(phase_tile_kernel<uint32_t, 4>,
+  if (cudaFuncSetAttribute(phase_tile_kernel<uint32_t, 4, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
       cudaFuncSetAttribute(phase_tile_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            bytes) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<uint32_t, 4>, 256,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<uint32_t, 4, false>, 256,
                                                     bytes) != cudaSuccess ||
       per_sm < 1 || sms < 1) {
     cudaGetLastError();
@@ -922,14 +964,18 @@ int tile_resident_grid() {
   return per_sm * sms;
 }
 
+// CTAs per SM of the single-tile kernel (48 registers; six at 40 registers
+// spilled more and measured slower).
+constexpr int kSmallMinB = 5;
+
 int tile_resident_grid_small() {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  constexpr int bytes = (int)sizeof(TileSmem<uint16_t>);
-  if (cudaFuncSetAttribute(phase_tile_kernel<uint16_t, 5>,
+  constexpr int bytes = (int)sizeof(TileSmem<uint16_t, 1>);
+  if (cudaFuncSetAttribute(phase_tile_kernel<uint16_t, kSmallMinB, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<uint16_t, 5>, 256,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<uint16_t, kSmallMinB, true>, 256,
                                                     bytes) != cudaSuccess ||
       per_sm < 1 || sms < 1) {
     cudaGetLastError();
@@ -951,11 +997,11 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
     // A phase that fits one wave of the compact kernel (one tile per CTA)
     // takes it: measured faster for several such lattices on their own streams.
     if (cfg.tile_grid_small > 0 && tiles <= cfg.tile_grid_small)
-      return launch_pdl_smem(phase_tile_kernel<uint16_t, 5>, (int)tiles, 256,
-                             sizeof(TileSmem<uint16_t>), s, g, (const uint16_t *)t.thrhi16,
+      return launch_pdl_smem(phase_tile_kernel<uint16_t, kSmallMinB, true>, (int)tiles, 256,
+                             sizeof(TileSmem<uint16_t, 1>), s, g, (const uint16_t *)t.thrhi16,
                              t.thr32, p_off, round_keys(g.k0, g.k1));
     const int grid = (int)(tiles < cfg.tile_grid ? tiles : cfg.tile_grid);
-    return launch_pdl_smem(phase_tile_kernel<uint32_t, 4>, grid, 256, sizeof(TileSmem<uint32_t>),
+    return launch_pdl_smem(phase_tile_kernel<uint32_t, 4, false>, grid, 256, sizeof(TileSmem<uint32_t>),
                            s, g, (const uint32_t *)t.thrhi, t.thr32, p_off,
                            round_keys(g.k0, g.k1));
   }
