@@ -53,10 +53,10 @@ OBS_EVERY = {"temperature4096": 10, "large16384": 1}
 # They hold only for the kernel sources they were taken with (kernel_digest);
 # after any change to those sources the bench reports them as null.
 PHASE_COUNTERS = {
-    "large16384": {"digest": "5b69eb7ff739d58e95fc549f9c6ef402c129c4e7dd6eac21b909c73f120c400b",
-                   "traffic": 33_652_736 + 13_056, "warp_inst": 30_210_381},
-    "temperature4096": {"digest": "5b69eb7ff739d58e95fc549f9c6ef402c129c4e7dd6eac21b909c73f120c400b",
-                        "traffic": 2_192_128, "warp_inst": 2_391_269},
+    "large16384": {"digest": "120d38af0d7a1b4eb54a9e80eb46a3e5110d63251cc6cdfd73aa94707cf29b32",
+                   "traffic": 33_654_272 + 29_440, "warp_inst": 30_243_157},
+    "temperature4096": {"digest": "120d38af0d7a1b4eb54a9e80eb46a3e5110d63251cc6cdfd73aa94707cf29b32",
+                        "traffic": 2_156_800, "warp_inst": 2_189_159},
 }
 # (file, first line, end line): the sources that define the tile phase kernel
 # and its launch -- ccmc_phase.cu from the per-word code through the tile
@@ -189,6 +189,16 @@ def tile_ok(s) -> bool:
     with W a multiple of 4 dividing 256, and Ly/4 a multiple of 256/W)."""
     W = (s.Lx // 4 + 15) // 16
     return (s.Lx // 4) % 16 == 0 and W % 4 == 0 and 256 % W == 0 and (s.Ly // 4) % (256 // W) == 0
+
+
+def tile_kernel_name(s) -> str:
+    """The tile-staged phase kernel a lattice takes: the single-tile compact
+    instantiation when its phase fits one wave of it (five CTAs per SM on the
+    152 SMs of a GB300), the pipelined one otherwise."""
+    W = (s.Lx // 4 + 15) // 16
+    tiles = (s.Ly // 4) // (256 // W)
+    return ("phase_tile_kernel<uint16_t, 5, single>" if tiles <= 5 * 152
+            else "phase_tile_kernel<uint32_t, 4>")
 
 
 def _dist():
@@ -592,7 +602,7 @@ def run_ours(args):
                          "traffic": counters["traffic"] if counters else None,
                          "issue": issue,
                          "kernel": f"colour phase of one {s0.Lx}^2 lattice "
-                                   f"({'phase_tile_kernel' if tile_ok(s0) else 'phase_kernel'})",
+                                   f"({tile_kernel_name(s0) if tile_ok(s0) else 'phase_kernel'})",
                          "peak_source": peak_kind, "launch_ms": phase_ms,
                          # the same algorithmic bytes over the whole timed region, every
                          # lattice's phases together (they overlap on their own streams)
