@@ -272,6 +272,15 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   if (tile_path_ok(g) && !std::getenv("CCMC_NO_TILE")) {
     h->cfg.tile_grid = tile_resident_grid();
     h->cfg.tile_grid_small = tile_resident_grid_small();
+    // CCMC_TILE_GRID=n (tests): the pipelined tile kernel with at most n CTAs,
+    // so that small lattices take several tiles per CTA
+    if (const char *e = std::getenv("CCMC_TILE_GRID")) {
+      const int n = std::atoi(e);
+      if (n > 0 && h->cfg.tile_grid > 0) {
+        h->cfg.tile_grid = n < h->cfg.tile_grid ? n : h->cfg.tile_grid;
+        h->cfg.tile_grid_small = 0;
+      }
+    }
   }
   while (((int64_t)1 << (2 * h->h)) < (int64_t)N) ++h->h;
   h->ring_cap = obs_capacity > 0 ? obs_capacity : 4096;

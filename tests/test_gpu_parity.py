@@ -249,39 +249,50 @@ def test_phase_steps_mixed_with_sweeps(cc):
         assert got[0, 0] == 3  # the record of the sweep the phases left open
 
 
-TILE_SHAPES = [(256, 256), (512, 128), (1024, 64), (2048, 32)]
+TILE_SHAPES = [(256, 256), (512, 128), (1024, 64), (2048, 32), (256, 4096), (512, 512),
+               (1024, 256)]
 
 
-def _lattice(cc, Lx, Ly, tile: bool):
-    """A lattice on the tile-staged phase path (bulk copies into shared memory)
-    or, with CCMC_NO_TILE set at creation, on the direct-window path."""
+def _lattice(cc, Lx, Ly, path: str):
+    """A lattice on one phase path, chosen by environment variables read at
+    creation: "tile" (the default: the single-tile kernel for phases that fit
+    one wave of it, else the pipelined one), "pipelined" (the pipelined tile
+    kernel on at most three CTAs, so that each takes several tiles and later
+    phases stage their first tile early) or "direct" (no staging)."""
     import os
 
-    if tile:
-        os.environ.pop("CCMC_NO_TILE", None)
-        return cc.Lattice(Lx, Ly)
-    os.environ["CCMC_NO_TILE"] = "1"
+    env = {"tile": {}, "pipelined": {"CCMC_TILE_GRID": "3"}, "direct": {"CCMC_NO_TILE": "1"}}[path]
+    for k in ("CCMC_NO_TILE", "CCMC_TILE_GRID"):
+        os.environ.pop(k, None)
+    os.environ.update(env)
     try:
         return cc.Lattice(Lx, Ly)
     finally:
-        os.environ.pop("CCMC_NO_TILE", None)
+        for k in env:
+            os.environ.pop(k, None)
 
 
 @pytest.mark.parametrize("shape", TILE_SHAPES)
-@pytest.mark.parametrize("tile", [True, False])
-def test_tile_and_direct_paths_match_oracle(cc, shape, tile):
+@pytest.mark.parametrize("path", ["tile", "pipelined", "direct"])
+def test_tile_and_direct_paths_match_oracle(cc, shape, path):
     Lx, Ly = shape
-    seed = 300 + Lx
+    seed = 300 + Lx + Ly
     params = (1 / 0.8, 0.1, 1.0, 1.0)
     st = oracle.init_constrained(Lx, Ly, seed, 0.05, 0.3)
-    with _lattice(cc, Lx, Ly, tile) as lat:
+    with _lattice(cc, Lx, Ly, path) as lat:
         lat.init_constrained(seed, 0.05, 0.3)
         for s in range(4):
             lat.sweep(1, *params, obs_every=1)
             st, rec = oracle_run(st, seed, s, 1, *params)
             got = lat.get_state()
-            assert np.array_equal(got, st), (shape, tile, s, first_difference(got, st))
+            assert np.array_equal(got, st), (shape, path, s, first_difference(got, st))
         assert np.array_equal(lat.obs_series()[-1], rec[-1])
+        # a multi-sweep call replays the captured graph of phases (the early
+        # staging runs in graphs too)
+        lat.sweep(16, *params, obs_every=0)
+        st, _ = oracle_run(st, seed, 4, 16, *params)
+        got = lat.get_state()
+        assert np.array_equal(got, st), (shape, path, "graph", first_difference(got, st))
 
 
 def _near_seed(Lx, Ly, want, max_phase=320):
@@ -302,7 +313,7 @@ def test_tile_path_nearest_neighbour_phases(cc, want):
     nsw = P // 8 + 1
     params = (1.3, -0.2, 1.0, 0.7)
     st = oracle.init_constrained(Lx, Ly, seed, 0.1, 0.4)
-    with _lattice(cc, Lx, Ly, True) as lat:
+    with _lattice(cc, Lx, Ly, "tile") as lat:
         lat.init_constrained(seed, 0.1, 0.4)
         lat.sweep(nsw, *params, obs_every=1)
         st, rec = oracle_run(st, seed, 0, nsw, *params)
