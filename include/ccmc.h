@@ -104,7 +104,10 @@ int ccmc_phases(ccmc_lattice *h, int64_t nphases, double beta, double Delta, dou
  * together in one persistent launch on the batch stream: each CTA keeps a
  * whole lattice and its tables in shared memory and runs all its sweeps,
  * taking lattices from a work queue largest first.  Larger lattices run the
- * per-phase path on their own streams at the same time.  Every lattice ends in
+ * per-phase path at the same time: eight or more of them at the same sweep
+ * count with fewer than 16384 class-row words a phase (below 2048^2) advance
+ * in lock step, one launch per phase for all of them on the batch stream; the
+ * others each on their own stream.  Every lattice ends in
  * exactly the state ccmc_sweep would give it (same random streams), and its
  * observable ring gets the same records.  Ordering: the batch waits for work
  * already queued on each lattice's stream, and each lattice's stream waits for
