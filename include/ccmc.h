@@ -251,6 +251,19 @@ int ccmc_recount_noalloc(const uint8_t *d_state, int Lx, int Ly, int64_t *d_out,
  * 5043 entries.  No GPU needed. */
 int ccmc_threshold_table(double beta, double Delta, double V, double J, uint32_t *out);
 
+/* Diagnostic (the paper has no counterpart): the bounded-wait self-test.  One
+ * CTA waits on a device barrier that nothing completes, giving up after
+ * `polls` polls (1 .. 2^24), records the timeout and returns, as every wait of
+ * the phase kernels does; the call then returns CCMC_E_TIMEOUT and the CUDA
+ * context stays usable.  Errors: E_INVAL (polls out of range), E_NOMEM,
+ * E_CUDA.  Host-side failures can be injected with the environment variable
+ * CCMC_FAULT (comma-separated): "alloc" makes ccmc_lattice_create and
+ * ccmc_batch_create return E_NOMEM before allocating anything, "launch" makes
+ * ccmc_sweep, ccmc_phases and ccmc_batch_sweep return E_CUDA before queuing
+ * anything (the handle stays usable), "admit" makes the server refuse every
+ * request at admission (result status E_BUDGET). */
+int ccmc_selftest_wait(uint32_t polls);
+
 /* Diagnostic: Philox4x32-10 on the device for counters (c0 + i, c1, c2, c3),
  * i < count, key (k0, k1); out receives 4 * count words (host buffer). */
 int ccmc_philox_device(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,

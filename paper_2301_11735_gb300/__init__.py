@@ -89,6 +89,7 @@ def _load():
         "ccmc_set_state_packed": (c_int, [vp, u8p, c_uint64, c_int64]),
         "ccmc_sync": (c_int, [vp]),
         "ccmc_philox_device": (c_int, [c_uint32] * 6 + [c_int64, u32p]),
+        "ccmc_selftest_wait": (c_int, [c_uint32]),
         "ccmc_batch_create": (c_int, [c_int, POINTER(vp), vp, POINTER(vp)]),
         "ccmc_batch_destroy": (c_int, [vp]),
         "ccmc_batch_config": (c_int, [vp, c_int, c_int64, c_int]),
@@ -155,6 +156,12 @@ def philox_device(ctr, key, count: int) -> np.ndarray:
                                    *[int(k) & 0xFFFFFFFF for k in key], count,
                                    out.ctypes.data_as(POINTER(c_uint32))), "ccmc_philox_device")
     return out.reshape(count, 4)
+
+
+def selftest_wait(polls: int = 1 << 16) -> int:
+    """The bounded-wait self-test: a device wait on a barrier nothing completes
+    gives up after `polls` polls; returns the call's code (E_TIMEOUT expected)."""
+    return lib().ccmc_selftest_wait(polls)
 
 
 def map_size(Lx: int, Ly: int) -> int:

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/ccmc.h"
+#include "ccmc_fault.h"
 #include "ccmc_internal.h"
 #include "ccmc_map.h"
 #include "ccmc_state.h"
@@ -256,6 +257,7 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   *out = nullptr;
   int rc = validate_shape(Lx, Ly);
   if (rc) return rc;
+  if (fault_injected("alloc")) return CCMC_E_NOMEM;
   ccmc_lattice *h = new (std::nothrow) ccmc_lattice();
   if (!h) return CCMC_E_NOMEM;
   Geo &g = h->g;
@@ -391,6 +393,7 @@ int ccmc_sweep(ccmc_lattice *h, int64_t nsweeps, double beta, double Delta, doub
   if (!(beta >= 0.0) || !std::isfinite(Delta) || !std::isfinite(V) || !std::isfinite(J))
     return CCMC_E_INVAL;
   if (!h->initialised) return CCMC_E_STATE;
+  if (fault_injected("launch")) return CCMC_E_CUDA;
   int rc = upload_params(h, beta, Delta, V, J);
   if (rc) return rc;
   if (nsweeps > 0 && h->phases_done % 8) {
@@ -425,6 +428,7 @@ int ccmc_phases(ccmc_lattice *h, int64_t nphases, double beta, double Delta, dou
   if (!(beta >= 0.0) || !std::isfinite(Delta) || !std::isfinite(V) || !std::isfinite(J))
     return CCMC_E_INVAL;
   if (!h->initialised) return CCMC_E_STATE;
+  if (fault_injected("launch")) return CCMC_E_CUDA;
   int rc = upload_params(h, beta, Delta, V, J);
   if (rc) return rc;
   for (int64_t p = 0; p < nphases; ++p) {
@@ -889,6 +893,7 @@ int ccmc_batch_create(int count, ccmc_lattice *const *lattices, void *cuda_strea
   *out = nullptr;
   for (int i = 0; i < count; ++i)
     if (!lattices[i]) return CCMC_E_INVAL;
+  if (ccmc::fault_injected("alloc")) return CCMC_E_NOMEM;
   const int rc = ccmc::batch_new(count, (cudaStream_t)cuda_stream, out);
   if (rc != CCMC_OK) return rc;
   (*out)->lats.assign(lattices, lattices + count);
@@ -975,6 +980,7 @@ int ccmc_batch_config(ccmc_batch *b, int resident_threads, int64_t resident_max_
 int ccmc_batch_sweep(ccmc_batch *b, const int64_t *nsweeps, const double *beta,
                      const double *Delta, const double *V, const double *J, int obs_every) {
   if (!b || !nsweeps || !beta || !Delta || !V || !J) return CCMC_E_INVAL;
+  if (ccmc::fault_injected("launch")) return CCMC_E_CUDA;
   std::vector<int> every(b->lats.size(), obs_every);
   return ccmc::batch_run(b, b->lats, nsweeps, beta, Delta, V, J, every.data(), true);
 }
@@ -987,6 +993,21 @@ int ccmc_batch_sync(ccmc_batch *b) {
     if (rc) return rc;
   }
   return CCMC_OK;
+}
+
+int ccmc_selftest_wait(uint32_t polls) {
+  if (polls == 0 || polls > (1u << 24)) return CCMC_E_INVAL;
+  int *d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return CCMC_E_NOMEM;
+  int status = 0;
+  int rc = CCMC_OK;
+  if (cudaMemset(d, 0, sizeof(int)) != cudaSuccess ||
+      ccmc::launch_wait_selftest(polls, d, 0) != cudaSuccess ||
+      cudaMemcpy(&status, d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = CCMC_E_CUDA;
+  cudaFree(d);
+  if (rc) return rc;
+  return status ? CCMC_E_TIMEOUT : CCMC_OK;
 }
 
 int ccmc_philox_device(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,

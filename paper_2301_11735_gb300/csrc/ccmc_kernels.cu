@@ -8,6 +8,7 @@
 
 #include "ccmc_count.cuh"
 #include "ccmc_device.cuh"
+#include "ccmc_fault.h"
 #include "ccmc_internal.h"
 #include "ccmc_launch.cuh"
 #include "ccmc_state.h"
@@ -162,6 +163,38 @@ __global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
 __global__ void advance_kernel(int64_t *ctl, int64_t phases) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   ctl[kCtlPhaseBase] += phases;
+}
+
+// Self-test of the bounded device waits: one CTA waits on an mbarrier that
+// nothing completes, polling at most `polls` times, then records the timeout in
+// *status and returns -- as the phase kernels' waits do on a bulk copy or an
+// arrival that never comes, so that the context stays usable.
+__global__ void wait_selftest_kernel(uint32_t polls, int *status) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool done = false;
+  for (uint32_t i = 0; i < polls && !done; ++i) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"(a)
+        : "memory");
+    done = r != 0;
+  }
+  if (!done && threadIdx.x == 0) *status = 1;
+}
+
+cudaError_t launch_wait_selftest(uint32_t polls, int *status, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(polls, status);
+  return cudaGetLastError();
 }
 
 __global__ void set_ctl_kernel(int64_t *ctl, int64_t phase_base) {

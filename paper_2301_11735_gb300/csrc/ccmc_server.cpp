@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "../../include/ccmc.h"
+#include "ccmc_fault.h"
 #include "ccmc_internal.h"
 
 namespace {
@@ -140,7 +141,7 @@ void ccmc_server::run() {
       while (!queue.empty() && (int)(active.size() + admit.size()) < max_active) {
         Pending &p = queue.front();
         const size_t bytes = request_bytes(p.req);
-        if (bytes > budget) {  // can never fit
+        if (bytes > budget || ccmc::fault_injected("admit")) {  // can never fit
           Finished f{};
           f.res.status = CCMC_E_BUDGET;
           f.res.submit_s = p.t_submit;
