@@ -351,6 +351,45 @@ def measure_batched(cc, nsweeps=5000, plain_sample=32, plain_sweeps=200):
             "speedup_vs_plain": (work / dt) / plain}
 
 
+def measure_small(cc, reps=3):
+    """The 16x16 lattice of 48 + 16 charges (Delta = 0.5, V = J = 1, T = 1):
+    2000 sweeps with observables after every sweep, as microseconds a sweep on
+    the plain single-lattice path (eight phase launches and a recount a sweep,
+    replayed as graphs) and as a batch of one (one resident launch with the
+    lattice in shared memory, autotuned launch shape); best of reps, host clock
+    around a synchronised call."""
+    from workloads import SMALL_16 as c
+
+    beta, nsw = 1.0 / c["T"], c["nsweeps"]
+    out = {"workload": f"{c['L']}x{c['L']}, {c['n_plus']} + {c['n_minus']} charges, "
+                       f"Delta={c['Delta']}, V={c['V']}, J={c['J']}, T={c['T']}: {nsw} sweeps, "
+                       f"observables every sweep"}
+    with cc.Lattice(c["L"], c["L"]) as lat:
+        lat.init_counts(c["seed"], c["n_plus"], c["n_minus"])
+        lat.sweep(20, beta, c["Delta"], c["V"], c["J"], obs_every=1)
+        lat.sync()
+        best = float("inf")
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            lat.sweep(nsw, beta, c["Delta"], c["V"], c["J"], obs_every=1)
+            lat.sync()
+            best = min(best, time.perf_counter() - t0)
+        out["plain_us_per_sweep"] = 1e6 * best / nsw
+        with cc.Batch([lat]) as b:
+            out["batched_config"] = list(b.autotune(probe_sweeps=10))
+            cols = ([beta], [c["Delta"]], [c["V"]], [c["J"]])
+            b.sweep(20, *cols, obs_every=1)
+            b.sync()
+            best = float("inf")
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                b.sweep(nsw, *cols, obs_every=1)
+                b.sync()
+                best = min(best, time.perf_counter() - t0)
+        out["batched_us_per_sweep"] = 1e6 * best / nsw
+    return out
+
+
 def measure_paper_maps(cc, L=4096, nmaps=40, batch=8):
     """The paper's own parallel scheme (Sec. 3.2) on one lattice of the
     workload: maps of N/10 pairs built on the host by random marking (all host
@@ -616,6 +655,7 @@ def run_ours(args):
             line["batched"] = measure_batched(cc)
             line["served"] = measure_served(cc)
             line["paper_maps"] = measure_paper_maps(cc)
+            line["small16"] = measure_small(cc)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample(sims)
         print(json.dumps(line), flush=True)

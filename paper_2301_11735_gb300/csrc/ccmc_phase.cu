@@ -844,6 +844,13 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
     gs.words = s_words;
     const bool aligned = (g.Cx & 15) == 0;
     const int nwa = g.Cy * g.W;  // a-words per phase
+    // thread 0's copies of the record count and its ring slot: read once per
+    // job, so that a record costs no global load on the sweep's critical path
+    int64_t obs_cnt = 0, obs_slot = 0;
+    if (threadIdx.x == 0 && obs_every > 0) {
+      obs_cnt = g.ctl[kCtlObsCount];
+      obs_slot = obs_cnt % J.ring_cap;
+    }
     __syncthreads();
     const int nwarps = blockDim.x >> 5;
     for (int64_t s = 0; s < nsweeps; ++s) {
@@ -890,14 +897,17 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
             rec[1 + k] = v;
           }
           for (int k = 0; k < 8; ++k) g.ctl[kCtlLatest + k] = rec[k];
-          const int64_t cnt = g.ctl[kCtlObsCount];
-          int64_t *dst = J.ring + (cnt % J.ring_cap) * 8;
+          int64_t *dst = J.ring + obs_slot * 8;
           for (int k = 0; k < 8; ++k) dst[k] = rec[k];
-          g.ctl[kCtlObsCount] = cnt + 1;
-          if (J.hist) {
+          g.ctl[kCtlObsCount] = ++obs_cnt;
+          if (++obs_slot == J.ring_cap) obs_slot = 0;
+          if (J.hist) {  // reductions: no load to wait for
             const int64_t N = (int64_t)g.Lx * g.Ly;
             const int64_t vals[3] = {rec[4], rec[5], rec[7]};
-            for (int h = 0; h < 3; ++h) J.hist[h * J.nbins + (vals[h] + N) * J.nbins / (2 * N + 1)] += 1;
+            for (int h = 0; h < 3; ++h)
+              atomicAdd(reinterpret_cast<unsigned long long *>(
+                            J.hist + h * J.nbins + (vals[h] + N) * J.nbins / (2 * N + 1)),
+                        1ull);
           }
         }
         __syncthreads();

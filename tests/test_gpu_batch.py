@@ -183,3 +183,39 @@ def test_large_lattices_in_lockstep_equal_individual_runs(cc, shapes):
             assert np.array_equal(one.get_state(), lat.get_state()), (Lx, Ly, T)
             assert np.array_equal(one.obs_series(), lat.obs_series()), (Lx, Ly, T)
         lat.close()
+
+
+def test_resident_records_wrap_the_ring_and_fill_histograms(cc):
+    """Lattices in the resident launch with a ring of 8 records and 32-bin
+    histograms: 2 calls x 7 sweeps with a record after every sweep wrap the
+    ring, and the ring and histograms equal those of the plain path."""
+    shapes = [(16, 16), (32, 32), (64, 32), (32, 8)]
+
+    def run(batched):
+        out = []
+        lats = []
+        for i, (Lx, Ly) in enumerate(shapes):
+            lat = cc.Lattice(Lx, Ly, obs_capacity=8)
+            lat.hist_enable(32)
+            lat.init_constrained(700 + i, [0.0, 0.1, -0.2, 0.3][i], 0.3)
+            lats.append(lat)
+        P = [_params(i) for i in range(len(shapes))]
+        for _ in range(2):
+            if batched:
+                with cc.Batch(lats) as b:
+                    b.sweep(7, [p[0] for p in P], [p[1] for p in P], [p[2] for p in P],
+                            [p[3] for p in P], obs_every=1)
+                    b.sync()
+            else:
+                for lat, p in zip(lats, P):
+                    lat.sweep(7, *p, obs_every=1)
+        for lat in lats:
+            out.append((lat.get_state(), lat.obs_series(), lat.hist()))
+            lat.close()
+        return out
+
+    got, ref = run(True), run(False)
+    for (s1, r1, h1), (s2, r2, h2), shape in zip(got, ref, shapes):
+        assert len(r1) == 8 and r1[-1, 0] == 14, shape
+        assert np.array_equal(s1, s2) and np.array_equal(r1, r2), shape
+        assert np.array_equal(h1, h2) and h1.sum() == 3 * 14, shape
