@@ -880,8 +880,11 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
       }
       const int64_t done = P0 / 8 + s + 1;
       if (obs_every > 0 && done % obs_every == 0) {
+        // the 16 classes side by side: thread t takes words t mod (blockDim / 16),
+        // ... of class 16 t / blockDim (blockDim a multiple of 16)
         int c[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int cls = 0; cls < 16; ++cls) count_class(gs, cls, threadIdx.x, blockDim.x, c);
+        const int per_cls = (int)blockDim.x >> 4;
+        count_class(gs, (int)threadIdx.x / per_cls, (int)threadIdx.x % per_cls, per_cls, c);
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
           const int64_t v = warp_sum((int64_t)c[k]);
