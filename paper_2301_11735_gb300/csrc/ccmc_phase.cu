@@ -822,6 +822,7 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
   uint2 *s_trans = reinterpret_cast<uint2 *>(dyn + kThrHiWords);
   uint32_t *s_words = dyn + kResTableWords;
   __shared__ Sched s_sched[8];  // the schedules of the current sweep's phases
+  __shared__ PhaseU s_u[8];     // and their class pointers and offsets
   __shared__ int s_job;
   __shared__ int64_t s_red[32][7];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -855,18 +856,21 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
     const int nwarps = blockDim.x >> 5;
     for (int64_t s = 0; s < nsweeps; ++s) {
       // the eight schedules of the sweep depend on nothing but the phase
-      // index: the warps draw them together, then every phase needs only the
-      // barrier that orders it after the previous one
+      // index: the warps draw them (and derive each phase's class pointers)
+      // together, then every phase needs only the barrier that orders it
+      // after the previous one
       for (int q = warp; q < 8; q += nwarps) {
         const Sched sc = draw_schedule(gs, (uint64_t)(P0 + 8 * s + q));
-        if (lane == 0) s_sched[q] = sc;
+        if (lane == 0) {
+          s_sched[q] = sc;
+          s_u[q] = phase_uniform(gs, sc);
+        }
       }
       __syncthreads();
       for (int p = 0; p < 8; ++p) {
         const uint64_t P = (uint64_t)(P0 + 8 * s + p);
-        const Sched sc = s_sched[p];
-        const PhaseU u = phase_uniform(gs, sc);
-        const uint32_t near128 = sc.near ? 128u : 0u;
+        const PhaseU &u = s_u[p];  // read from shared memory where used
+        const uint32_t near128 = s_sched[p].near ? 128u : 0u;
         for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
           const int j = wid / g.W, w = wid - j * g.W;
           if (aligned)
