@@ -808,6 +808,128 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
 }
 
 // ============================================================================
+// One group of phase_word: the pairs 4 b .. 4 b + 3 of a-word w (the four
+// pairs of one Philox call), for the resident kernel on lattices with at most a
+// quarter as many a-words a phase as threads.  Four threads then share a word,
+// each running a quarter of its pairs, which shortens the per-phase chain that
+// bounds such small lattices.  The random streams, fast and exact decisions are
+// phase_word's, so the results are identical; the a word is shared by the four
+// threads, so it is updated by XOR.  kMode: kRowAligned or kRowGeneral.
+template <int kMode>
+__device__ __forceinline__ void phase_group(const Geo &g, const PhaseU &u, const uint2 *trans,
+                                            const uint32_t *thrhi, const uint32_t *thr32, int j,
+                                            int w, int b, uint64_t P, uint32_t near128) {
+  static_assert(kMode != kRowTile, "rows of global or resident memory only");
+  constexpr bool kAligned = kMode != kRowGeneral;
+  const int s0 = w << 4;
+  const int n = kAligned ? 16 : min(16, g.Cx - s0);
+  const int nv = min(4, n - 4 * b);  // pairs of the group inside the row
+  if (nv <= 0) return;
+
+  // ---- gather, pair states and group lanes as in phase_word
+  uint32_t *rowA = const_cast<uint32_t *>(u.cA) + j * g.W;
+  const uint32_t A = rowA[w];
+  const int jb = wrap(j + u.qy, g.Cy);
+  const uint32_t B = window<kMode>(u.cB, g, u, jb, w, u.offB, n);
+  const Sums sa = neighbour_sums(window<kMode>(u.cAL, g, u, j, w, u.offAL, n),
+                                 window<kMode>(u.cAR, g, u, j, w, u.offAR, n),
+                                 u.cAU[wrap(j + u.dyAU, g.Cy) * g.W + w],
+                                 u.cAD[wrap(j + u.dyAD, g.Cy) * g.W + w]);
+  const Sums sb = neighbour_sums(window<kMode>(u.cBL, g, u, jb, w, u.offBL, n),
+                                 window<kMode>(u.cBR, g, u, jb, w, u.offBR, n),
+                                 window<kMode>(u.cBU, g, u, wrap(jb + u.dyBU, g.Cy), w, u.offB, n),
+                                 window<kMode>(u.cBD, g, u, wrap(jb + u.dyBD, g.Cy), w, u.offB, n));
+  const uint32_t pcE = ((A & 0x33333333u) << 2) | (B & 0x33333333u);
+  const uint32_t pcO = (A & 0xCCCCCCCCu) | ((B >> 2) & 0x33333333u);
+  GroupEnv ge;
+  uint32_t pck[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t d8 = group_bytes(sa.se, sa.so, k) + 0x08080808u - group_bytes(sb.se, sb.so, k);
+    const uint32_t ga = group_bytes(sa.ge, sa.go, k);
+    ge.gb[k] = group_bytes(sb.ge, sb.go, k);
+    ge.x01[k] = prmt(d8, ga, 0x5140u);
+    ge.x23[k] = prmt(d8, ga, 0x7362u);
+    pck[k] = group_bytes(pcE, pcO, k) * 8u + near128 * 0x01010101u;
+  }
+
+  // ---- the group's four pairs (pair_env's selector for a run-time b)
+  const uint32_t gbase = (uint32_t)j * (uint32_t)g.Cx4 + (uint32_t)(4 * w);
+  const uint32_t env_sel = 0x8410u + ((b & 1) ? 0x0122u : 0u) + ((b & 2) ? 0x0200u : 0u);
+  const U4 r = philox(gbase + (uint32_t)b, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
+  uint32_t accE = 0u, accO = 0u;
+  uint32_t mn = 0xFFFFFFFFu, mx = 0u, d0 = 0xFFFFFFFFu, v0 = 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!kAligned && k >= nv) {
+      if (k & 1) {
+        mn = min(mn, d0);
+        mx = max(mx, v0);
+      }
+      continue;
+    }
+    const uint32_t R = k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w;
+    const uint32_t env = prmt(b < 2 ? ge.x01[k] : ge.x23[k], ge.gb[k], env_sel);
+    const uint32_t pc8 = prmt(pck[k], 0u, 0x4440u + (uint32_t)b);
+    const uint32_t v = R & 0xFFFFu;
+    const uint2 e = move_entry(trans, mod12(v), pc8);
+    const uint32_t TH = thr_top(thrhi, __dp4a((int)e.y, (int)env, (int)e.x));
+    const uint32_t d = R - TH;
+    if (k & 1) {
+      mn = __vimin3_u32(mn, d0, d);
+      mx = __vimax3_u32(mx, v0, v);
+    } else {
+      d0 = d;
+      v0 = v;
+    }
+    const uint32_t xm = R < TH ? (e.y & 0xF0000000u) : 0u;
+    if (k & 1)
+      accO = (accO >> 4) | xm;
+    else
+      accE = (accE >> 4) | xm;
+  }
+  const uint32_t slow = (mn < 0x10000u || mx >= 65532u) ? 0xFu << (4 * b) : 0u;
+  // the group's even pairs 4b, 4b+2 (odd 4b+1, 4b+3) belong in lanes 2b, 2b+1
+  // of accE (accO); the pe (po) shifted in sit in the top lanes
+  const int pe = (nv + 1) >> 1, po = nv >> 1;
+  accE >>= 4 * (8 - pe - 2 * b);
+  accO = po == 0 ? 0u : accO >> (4 * (8 - po - 2 * b));
+  uint32_t dA = ((accE >> 2) & 0x33333333u) | (((accO >> 2) & 0x33333333u) << 2);
+  uint32_t dB = (accE & 0x33333333u) | ((accO & 0x33333333u) << 2);
+  if (slow) {
+    const uint2 dd = exact_path<kAligned>(trans, thrhi, thr32, g.k0, g.k1, gbase,
+                                          (uint32_t)((uint64_t)j * g.Cx + s0), n, P, near128, A,
+                                          B, sa, sb, slow, dA, dB);
+    dA = dd.x;
+    dB = dd.y;
+  }
+  if constexpr (!kAligned) {
+    if (n < 16) {
+      const uint32_t valid = (1u << (2 * n)) - 1u;
+      dA &= valid;
+      dB &= valid;
+    }
+  }
+
+  // ---- write back: the a word is shared with the word's other groups
+  if (dA) atomicXor(rowA + w, dA);
+  if (dB) {
+    uint32_t *rb = const_cast<uint32_t *>(u.cB) + jb * g.W;
+    if constexpr (kAligned) {
+      const int wl = wrap(w + (u.offB >> 4), g.W);
+      const int sh = 2 * (u.offB & 15);
+      atomicXor(rb + wl, dB << sh);
+      if (sh) {
+        const uint32_t hi = dB >> (32 - sh);
+        if (hi) atomicXor(rb + (wl + 1 == g.W ? 0 : wl + 1), hi);
+      }
+    } else {
+      scatter_xor(rb, g.Cx, wrap(s0 + u.offB, g.Cx), n, dB);
+    }
+  }
+}
+
+// ============================================================================
 // Resident batch kernel (many lattices of uneven size, one persistent launch).
 // Each CTA takes lattices from a work queue, largest first; it holds the whole
 // packed lattice and its tables in shared memory and runs all of that lattice's
@@ -815,7 +937,7 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
 // when due; then it writes the lattice back and takes the next one.  The same
 // per-word code as phase_kernel runs against shared memory, so results are
 // identical to the per-phase launches.
-__global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(256, 2) resident_kernel(const JobDesc *__restrict__ jobs, int njobs,
                                                        int *queue) {
   extern __shared__ __align__(16) uint32_t dyn[];
   uint32_t *s_thrhi = dyn;
@@ -845,6 +967,9 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
     gs.words = s_words;
     const bool aligned = (g.Cx & 15) == 0;
     const int nwa = g.Cy * g.W;  // a-words per phase
+    // four threads a word (one group of four pairs each) when there are threads
+    // enough, otherwise one word a thread
+    const bool grouped = 4 * nwa <= (int)blockDim.x;
     // thread 0's copies of the record count and its ring slot: read once per
     // job, so that a record costs no global load on the sweep's critical path
     int64_t obs_cnt = 0, obs_slot = 0;
@@ -871,14 +996,25 @@ __global__ void __launch_bounds__(256) resident_kernel(const JobDesc *__restrict
         const uint64_t P = (uint64_t)(P0 + 8 * s + p);
         const PhaseU &u = s_u[p];  // read from shared memory where used
         const uint32_t near128 = s_sched[p].near ? 128u : 0u;
-        for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
-          const int j = wid / g.W, w = wid - j * g.W;
-          if (aligned)
-            phase_word<kRowAligned>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128,
-                                    SeedKeys{gs.k0, gs.k1});
-          else
-            phase_word<kRowGeneral>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128,
-                                    SeedKeys{gs.k0, gs.k1});
+        if (grouped) {
+          if ((int)threadIdx.x < 4 * nwa) {
+            const int wid = threadIdx.x >> 2, b = threadIdx.x & 3;
+            const int j = wid / g.W, w = wid - j * g.W;
+            if (aligned)
+              phase_group<kRowAligned>(gs, u, s_trans, s_thrhi, J.thr32, j, w, b, P, near128);
+            else
+              phase_group<kRowGeneral>(gs, u, s_trans, s_thrhi, J.thr32, j, w, b, P, near128);
+          }
+        } else {
+          for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
+            const int j = wid / g.W, w = wid - j * g.W;
+            if (aligned)
+              phase_word<kRowAligned>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128,
+                                      SeedKeys{gs.k0, gs.k1});
+            else
+              phase_word<kRowGeneral>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128,
+                                      SeedKeys{gs.k0, gs.k1});
+          }
         }
         __syncthreads();
       }
