@@ -25,7 +25,7 @@ DEFAULT = (256, 1 << 17, 2)
 CANDIDATES = [
     (threads, resident, ctas)
     for threads in (128, 256)
-    for resident in (1 << 12, 1 << 17)
+    for resident in (1 << 12, 1 << 14, 1 << 17)
     for ctas in (2, 4)
 ] + [(64, 1 << 17, 2)]
 
