@@ -4,7 +4,7 @@ Every comparison is bit-exact: lattice states, integer energy terms, the
 charge sum (which must equal n N after every sweep), schedules and random
 words.  Shapes cover several tiles of 16 sites, ragged row tails (Lx/4 not a
 multiple of 16 or of 4), rows shorter than one word, and the full sizes of the
-4096^2 and 16384^2 workloads (sampled or single-sweep there).
+4096^2 and 16384^2 workloads (their first 20 and 5 sweeps).
 """
 import numpy as np
 import pytest
@@ -175,51 +175,71 @@ def test_histograms_follow_the_records(cc):
 @pytest.mark.parametrize("T", [0.5, 2.0])
 def test_full_size_4096_first_sweeps(cc, T):
     """The 4096^2 workload (Delta = 0, V = 0.5, J = 1, n = 0.1, charged
-    fraction 0.3): identical initial state and identical lattice and records
-    after each of the first three sweeps."""
+    fraction 0.3): identical initial state, and identical lattice after each of
+    the first 20 sweeps and records of every sweep."""
     L, seed = 4096, 20
     st = oracle.init_constrained(L, L, seed, 0.1, 0.3)
     with cc.Lattice(L, L) as lat:
         lat.init_constrained(seed, 0.1, 0.3)
         assert np.array_equal(lat.get_state(), st)
-        for s in range(3):
+        recs = []
+        for s in range(20):
             lat.sweep(1, 1.0 / T, 0.0, 0.5, 1.0, obs_every=1)
             st, rec = oracle_run(st, seed, s, 1, 1.0 / T, 0.0, 0.5, 1.0)
-            assert np.array_equal(lat.get_state(), st), s
-        assert np.array_equal(lat.obs_series()[-1], rec[-1])
-        assert rec[-1][6] == 1677722
+            recs.append(rec[-1])
+            got = lat.get_state()
+            assert np.array_equal(got, st), (s, first_difference(got, st))
+        assert np.array_equal(lat.obs_series(), np.array(recs))
+        assert all(r[6] == 1677722 for r in recs)
 
 
-def test_full_size_16384_sampled_init_and_one_sweep(cc):
-    """The 16384^2 workload: the initial state is checked on sampled sites
-    (oracle rank of each sampled site), then one GPU sweep from that state is
-    compared with one oracle sweep from the same state."""
+def test_full_size_16384_first_sweeps(cc):
+    """The 16384^2 workload (Delta = 0.2, V = 1, J = 0.5, n = 0.05, T = 0.6):
+    the oracle's own initial state (every site) and the lattice and records
+    after each of the first five sweeps."""
     L, seed = 16384, 5
-    N = L * L
-    Q, npl, nmi = oracle.charge_counts(N, 0.05, 0.3)
+    params = (1 / 0.6, 0.2, 1.0, 0.5)
+    Q, npl, nmi = oracle.charge_counts(L * L, 0.05, 0.3)
+    st = oracle.init_constrained(L, L, seed, 0.05, 0.3)
+    counts = np.bincount(st.ravel(), minlength=4)
+    assert counts[2] == npl and counts[3] == nmi
     with cc.Lattice(L, L) as lat:
         lat.init_constrained(seed, 0.05, 0.3)
-        st = lat.get_state()
-        counts = np.bincount(st.ravel(), minlength=4)
-        assert counts[2] == npl and counts[3] == nmi
-        rng = np.random.default_rng(0)
-        key = oracle.seed_key(seed)
-        for i in rng.integers(0, N, size=2000):
-            r = oracle.feistel_rank(seed, N, int(i))
-            if r < npl:
-                exp = 2
-            elif r < npl + nmi:
-                exp = 3
-            else:
-                w = oracle.philox([int(i) >> 7, 0, 0, oracle.TAG_SIGN], key)
-                exp = int((w[(int(i) >> 5) & 3] >> (int(i) & 31)) & 1)
-            assert st.flat[i] == exp, i
-        lat.sweep(1, 1 / 0.6, 0.2, 1.0, 0.5, obs_every=1)
+        assert np.array_equal(lat.get_state(), st)
+        for s in range(5):
+            lat.sweep(1, *params, obs_every=1)
+            st, rec = oracle_run(st, seed, s, 1, *params)
+            got = lat.get_state()
+            assert np.array_equal(got, st), (s, first_difference(got, st))
+            assert np.array_equal(lat.obs_series()[-1], rec[-1]), s
+            assert rec[-1][6] == Q
+
+
+@pytest.mark.parametrize("path", ["plain", "batch"])
+@pytest.mark.parametrize("shape", [(64, 48), (256, 256), (36, 44)])
+def test_resume_across_the_phase_counter_high_word(cc, shape, path):
+    """A state resumed at sweep 2^29 - 1: its eight phases end at global phase
+    2^32 - 1 and the next sweep's start at 2^32, so the schedule and move
+    streams take the counter's high word (Philox counter word 2) from 0 to 1.
+    The state is drawn by the seeded test generator, not by either side."""
+    Lx, Ly = shape
+    seed, sweep0 = 31 + Lx, (1 << 29) - 1
+    params = (1 / 0.8, 0.1, 1.0, 0.5)
+    rng = np.random.default_rng(Lx * Ly)
+    st = rng.integers(0, 4, size=(Ly, Lx)).astype(np.uint8)
+    exp, erec = oracle_run(st, seed, sweep0, 3, *params)
+    assert erec[-1][0] == sweep0 + 3
+    with cc.Lattice(Lx, Ly) as lat:
+        lat.set_state(st, seed, sweep0)
+        if path == "plain":
+            lat.sweep(3, *params, obs_every=1)
+        else:
+            with cc.Batch([lat]) as b:
+                b.sweep(3, *([p] for p in params), obs_every=1)
+                b.sync()
         got = lat.get_state()
-        oracle_run_state, rec = oracle_run(st, seed, 0, 1, 1 / 0.6, 0.2, 1.0, 0.5)
-        assert np.array_equal(got, oracle_run_state)
-        assert np.array_equal(lat.obs_series()[-1], rec[-1])
-        assert rec[-1][6] == Q
+        assert np.array_equal(got, exp), first_difference(got, exp)
+        assert np.array_equal(lat.obs_series(), erec)
 
 
 def test_phase_steps_mixed_with_sweeps(cc):
