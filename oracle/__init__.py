@@ -42,6 +42,7 @@ def lib():
         ip, i32p = POINTER(c_int), POINTER(c_int32)
         sig = {
             "oracle_philox4x32_10": (None, [u32p, u32p, u32p]),
+            "oracle_philox_block": (None, [u32p, u32p, c_int64, u32p]),
             "oracle_charge_counts": (c_int, [c_int64, c_double, c_double, i64p, i64p, i64p]),
             "oracle_feistel_rank": (c_int64, [c_uint64, c_int64, c_int64]),
             "oracle_init_counts": (c_int, [c_int, c_int, c_uint64, c_int64, c_int64, u8p]),
@@ -100,6 +101,15 @@ def philox(ctr, key) -> np.ndarray:
     out = np.zeros(4, dtype=np.uint32)
     lib().oracle_philox4x32_10(_p(c, c_uint32), _p(k, c_uint32), _p(out, c_uint32))
     return out
+
+
+def philox_block(ctr, key, count: int) -> np.ndarray:
+    """(count, 4) outputs for counters (ctr[0] + i mod 2^32, ctr[1], ctr[2], ctr[3])."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4 * count, dtype=np.uint32)
+    lib().oracle_philox_block(_p(c, c_uint32), _p(k, c_uint32), count, _p(out, c_uint32))
+    return out.reshape(count, 4)
 
 
 def charge_counts(N: int, n: float, c: float = 0.3):

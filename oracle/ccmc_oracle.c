@@ -51,6 +51,16 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
   out[3] = x3;
 }
 
+/* A block of counters (ctr[0] + i mod 2^32, ctr[1], ctr[2], ctr[3]), i < count:
+ * out receives 4 * count words, one call of the generator each. */
+void oracle_philox_block(const uint32_t ctr[4], const uint32_t key[2], int64_t count,
+                         uint32_t *out) {
+  for (int64_t i = 0; i < count; ++i) {
+    const uint32_t c[4] = {ctr[0] + (uint32_t)i, ctr[1], ctr[2], ctr[3]};
+    oracle_philox4x32_10(c, key, out + 4 * i);
+  }
+}
+
 static void seed_key(uint64_t seed, uint32_t key[2]) {
   key[0] = (uint32_t)(seed & 0xFFFFFFFFu);
   key[1] = (uint32_t)(seed >> 32);

@@ -53,6 +53,9 @@ extern "C" {
 
 /* Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11). */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Counters (ctr[0] + i mod 2^32, ctr[1], ctr[2], ctr[3]) for i < count, in order. */
+void oracle_philox_block(const uint32_t ctr[4], const uint32_t key[2], int64_t count,
+                         uint32_t *out);
 
 /* Charge counts from (n, c): Q = llround(n N), C = max(llround(c N), |Q|),
  * C += 1 when C - Q is odd; N+ = (C + Q)/2, N- = (C - Q)/2.  Returns 0, or -1

@@ -28,6 +28,17 @@ def cc():
     return cc
 
 
+@pytest.mark.parametrize("ctr,key", [((0xFF800000, 7, 9, 2), (0xDEADBEEF, 0x12345678)),
+                                     ((0, 0xFFFFFFFF, 1, 0x4D4F5645), (5, 0))])
+def test_device_philox_matches_oracle_on_2_to_the_24_counters(cc, ctr, key):
+    """Every output of 2^24 consecutive counters (the first set wraps word 0
+    through 2^32), bit for bit."""
+    n = 1 << 24
+    dev = cc.philox_device(ctr, key, n)
+    ref = oracle.philox_block(ctr, key, n)
+    assert np.array_equal(dev, ref), first_difference(dev, ref)
+
+
 def test_device_philox_matches_oracle(cc):
     for ctr, key in [((0, 0, 0, 0), (0, 0)), ((0xFFFFFF00, 7, 9, 2), (0xDEADBEEF, 0x12345678)),
                      ((123, 0xFFFFFFFF, 0, 5), (1, 0))]:

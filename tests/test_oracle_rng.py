@@ -48,3 +48,13 @@ def test_philox_words_are_uniform():
     bits = ((w[:, None] >> np.arange(32, dtype=np.uint64)) & 1).mean(axis=0)
     sigma = 0.5 / np.sqrt(len(w))
     assert np.all(np.abs(bits - 0.5) < 5 * sigma)
+
+
+def test_philox_block_is_the_generator_counter_by_counter():
+    """The block form (used for bulk device comparisons) is the single-call
+    generator at counters ctr[0] + i, wrapping at 2^32 in word 0 only."""
+    ctr, key = [0xFFFFFFF0, 7, 9, 2], [0xDEADBEEF, 0x12345678]
+    b = oracle.philox_block(ctr, key, 64)
+    for i in range(64):
+        c = [(ctr[0] + i) & 0xFFFFFFFF] + ctr[1:]
+        assert np.array_equal(b[i], oracle.philox(c, key)), i
