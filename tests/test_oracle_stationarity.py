@@ -12,6 +12,8 @@ This pins the oracle to that property on every constrained state of the 4x4
 torus at Q = +-13 (4960 states each), for four pairs (two bonded, a diagonal
 and a distant one): with the move's 16-bit choice field v taken through all
 twelve classes v mod 12 (each equally likely, as 65532 = 12 x 5461),
+  * the proposal is uniform over the pair's q-set (the current configuration
+    included) and frozen for |q| = 2,
   * every proposal x -> y is matched by y -> x with the same multiplicity, and
   * pi(x) A(x -> y) and pi(y) A(y -> x) agree to within 2^-32 max(pi(x), pi(y)),
     the rounding of the acceptance table (thresholds floored to 2^-32).
@@ -83,9 +85,14 @@ def test_pair_move_is_reversible_on_every_constrained_4x4_state(Q):
         acc = {}   # (x, y) -> acceptance probability of the move
         for x in states:
             kx = x.tobytes()
+            q = int(x.flat[a] >= 2) * (5 - 2 * int(x.flat[a])) + \
+                int(x.flat[b] >= 2) * (5 - 2 * int(x.flat[b]))  # S_a + S_b
+            per_y = {}
             for v in range(12):
                 y = x.copy()
-                if not oracle.pair_move(y, a, b, v, key, ctr, accept_all):
+                moved = oracle.pair_move(y, a, b, v, key, ctr, accept_all)
+                per_y[y.tobytes()] = per_y.get(y.tobytes(), 0) + 1
+                if not moved:
                     continue  # frozen pair or the current configuration drawn
                 ky = y.tobytes()
                 assert ky in E, "a move left the constrained set"
@@ -93,6 +100,11 @@ def test_pair_move_is_reversible_on_every_constrained_4x4_state(Q):
                 d = oracle.pair_delta(x, a, b, int(y.flat[a]), int(y.flat[b]))
                 thr = int(table.reshape(-1)[lib.oracle_table_index(*d)])
                 acc[kx, ky] = 1.0 if thr == 0xFFFFFFFF else thr / 2.0 ** 32
+            # the proposal is uniform over the pair's q-set, the current
+            # configuration included: 4 (|q| = 1) or 6 (q = 0) outcomes, each
+            # from 12 / |set| of the choice classes; |q| = 2 cannot move
+            nset = {2: 1, 1: 4, 0: 6}[abs(q)]
+            assert sorted(per_y.values()) == [12 // nset] * nset, (a, b, q, per_y.values())
         assert mult, (a, b)
         for (kx, ky), m in mult.items():
             assert mult.get((ky, kx)) == m, ("proposals not symmetric", a, b)
