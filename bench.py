@@ -15,12 +15,13 @@ every step uploads the lattices from pinned host memory in the compact form,
 2 bits a site (ccmc_set_state_packed, stream-ordered), and reads the
 observable records back (ccmc_obs_series).
 
-Beside the headline the same JSON line carries more measurements of the
-spec patterns: `paper_maps` (the paper's own host-built maps against the
-colour schedule), `batched` (512 replicas of uneven L in one persistent
-launch, against back-to-back single-lattice launches) and `served` (a Poisson
-request stream through the continuous-batching server: p50/p99 latency,
-achieved vs offered site-updates/s, against back-to-back plain runs).
+Beside the headline the same JSON line carries more measurements: `paper_maps`
+(the paper's own host-built maps against the colour schedule), `batched` (512
+replicas of uneven L in one persistent launch, against back-to-back
+single-lattice launches), `served` (a Poisson request stream through the
+continuous-batching server: p50/p99 latency, achieved vs offered
+site-updates/s, against back-to-back plain runs) and `small16` (the 16x16
+lattice's microseconds a sweep, plain and as a batch of one).
 
 `--impl reference` times the CPU oracle (single-threaded C) on a bounded sample
 of the same workload.  Under torchrun each rank runs its own four lattices
