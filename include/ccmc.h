@@ -264,8 +264,10 @@ int ccmc_threshold_table(double beta, double Delta, double V, double J, uint32_t
  * request at admission (result status E_BUDGET). */
 int ccmc_selftest_wait(uint32_t polls);
 
-/* Diagnostic: Philox4x32-10 on the device for counters (c0 + i, c1, c2, c3),
- * i < count, key (k0, k1); out receives 4 * count words (host buffer). */
+/* Diagnostic: Philox4x32-10 on the device for counters (c0 + i mod 2^32, c1,
+ * c2, c3), i < count, key (k0, k1); out receives 4 * count words (host buffer
+ * owned by the caller), counter by counter.  Synchronous on the default stream.
+ * Errors: E_INVAL (out NULL, count < 0 or count > 2^28), E_NOMEM, E_CUDA. */
 int ccmc_philox_device(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                        uint32_t k1, int64_t count, uint32_t *out);
 
