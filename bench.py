@@ -59,6 +59,13 @@ PHASE_COUNTERS = {
     "temperature4096": {"digest": "120d38af0d7a1b4eb54a9e80eb46a3e5110d63251cc6cdfd73aa94707cf29b32",
                         "traffic": 2_156_800, "warp_inst": 2_189_159},
 }
+# What bounds the dominant kernel, from the same captures: the HBM roofline is
+# the algorithm's bound, these are the kernel's.
+PHASE_LIMITER = {
+    "large16384": "integer instruction issue (DRAM throughput 9 %, issue active 62 %, "
+                  "ALU pipe 55 %)",
+    "temperature4096": "latency (issue active 32 %, 3.2 warps a scheduler; one word a thread)",
+}
 # (file, first line, end line): the sources that define the tile phase kernel
 # and its launch -- ccmc_phase.cu from the per-word code through the tile
 # kernel, and its launchers; the headers whole.
@@ -641,6 +648,7 @@ def run_ours(args):
                          "frac": achieved / peak,
                          "traffic": counters["traffic"] if counters else None,
                          "issue": issue,
+                         "limiter": PHASE_LIMITER.get(args.workload) if counters else None,
                          "kernel": f"colour phase of one {s0.Lx}^2 lattice "
                                    f"({tile_kernel_name(s0) if tile_ok(s0) else 'phase_kernel'})",
                          "peak_source": peak_kind, "launch_ms": phase_ms,
