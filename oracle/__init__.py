@@ -51,6 +51,7 @@ def lib():
             "oracle_offset_allowed": (c_int, [c_int, c_int, c_int, c_int]),
             "oracle_schedule": (None, [c_int, c_int, c_uint64, c_uint64, ip, ip, ip, ip]),
             "oracle_pair_delta": (None, [u8p, c_int, c_int, c_int, c_int, c_int, c_int, ip]),
+            "oracle_site_delta": (None, [u8p, c_int, c_int, c_int, c_int, ip]),
             "oracle_pair_move": (c_int, [u8p, c_int, c_int, c_int, c_int, c_uint32, u32p, u32p,
                                          u32p]),
             "oracle_recount": (None, [u8p, c_int, c_int, i64p]),
@@ -160,6 +161,14 @@ def pair_delta(st: np.ndarray, a: int, b: int, na: int, nb: int):
     Ly, Lx = st.shape
     out = (c_int * 3)()
     lib().oracle_pair_delta(_u8(st), Lx, Ly, a, b, na, nb, out)
+    return tuple(out)
+
+
+def site_delta(st: np.ndarray, a: int, nc: int):
+    """(dNc, dBV, dBJ) of Eq. 3 when site a alone takes code nc."""
+    Ly, Lx = st.shape
+    out = (c_int * 3)()
+    lib().oracle_site_delta(_u8(st), Lx, Ly, a, nc, out)
     return tuple(out)
 
 

@@ -617,6 +617,26 @@ int64_t oracle_map_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t ma
 }
 
 /* ------------------------------------------------------------------------ */
+/* Single-site energy change (Eq. 3): only the terms of site a change; each of
+ * its bonds contributes the change of a's value times the neighbour's (old)
+ * value. */
+void oracle_site_delta(const uint8_t *st, int Lx, int Ly, int a, int nc, int out[3]) {
+  int c = st[a];
+  int nbr[4];
+  neighbours(Lx, Ly, a, nbr);
+  int sumS = 0, sumG = 0;
+  for (int k = 0; k < 4; ++k) {
+    sumS += CODE_S[st[nbr[k]]];
+    sumG += CODE_SIGMA[st[nbr[k]]];
+  }
+  int dS = CODE_S[nc] - CODE_S[c];
+  int dG = CODE_SIGMA[nc] - CODE_SIGMA[c];
+  out[0] = CODE_S[nc] * CODE_S[nc] - CODE_S[c] * CODE_S[c];
+  out[1] = dS * sumS;
+  out[2] = dG * sumG;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Penalty-function baseline (Sec. 2.2): the charge is held near nN not by the
  * move but by a chemical-potential term -mu sum_i S_i added to the energy, with
  * mu adjusted as the run goes.  Single-site Metropolis: a uniformly chosen site
@@ -653,17 +673,10 @@ int64_t oracle_penalty_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_
       int a = (int)(uint64_t)(prod >> 64);
       int c = st[a];
       int nc = (c + 1 + (int)(w[2] % 3u)) & 3;
-      int nbr[4];
-      neighbours(Lx, Ly, a, nbr);
-      int sumS = 0, sumG = 0;
-      for (int k = 0; k < 4; ++k) {
-        sumS += CODE_S[st[nbr[k]]];
-        sumG += CODE_SIGMA[st[nbr[k]]];
-      }
+      int d[3];
+      oracle_site_delta(st, Lx, Ly, a, nc, d);
       int dS = CODE_S[nc] - CODE_S[c];
-      int dQ = CODE_S[nc] * CODE_S[nc] - CODE_S[c] * CODE_S[c];
-      int dG = CODE_SIGMA[nc] - CODE_SIGMA[c];
-      double dE = Delta * dQ + V * (double)(dS * sumS) + 0.25 * J * (double)(dG * sumG);
+      double dE = Delta * d[0] + V * (double)d[1] + 0.25 * J * (double)d[2];
       double dEp = dE - *mu * (double)dS;
       int accept = dEp <= 0.0 || ((double)w[3] * 0x1p-32) < exp(-beta * dEp);
       if (accept) {

@@ -129,12 +129,19 @@ int64_t oracle_map_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t ma
                           double beta, double Delta, double V, double J, int obs_every,
                           int64_t *records);
 
+/* Change of the integer energy terms (dNc, dBV, dBJ) of Eq. (3) when site a
+ * alone goes from its current code to code nc: dNc = S'^2 - S^2, dBV = dS x
+ * (sum of S over a's four neighbours), dBJ = dsigma x (sum of sigma over them),
+ * each neighbour counted once per bond (twice on a 2-wide torus). */
+void oracle_site_delta(const uint8_t *st, int Lx, int Ly, int a, int nc, int out[3]);
+
 /* Penalty-function baseline (Sec. 2.2): single-site Metropolis with the extra
  * energy -mu sum S, mu <- mu + kappa (nN - sum S)/N after every sweep (the
  * adjustment rule is this oracle's reading).  *mu is read and updated.
- * Parity unpinned: a mu-controlled chain has no exact reference; its test
- * checks the qualitative behaviour the paper reports (charge held on average
- * only, heat capacity growing as T -> 0).  It has no GPU counterpart. */
+ * Pinned by its single-site energy change against a full recount, and at
+ * kappa = 0 (fixed mu) by the exact grand-canonical averages of 3 x 3 and
+ * 4 x 2 tori; the adjustment rule itself has no exact reference.  It has no
+ * GPU counterpart. */
 int64_t oracle_penalty_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
                               int64_t nsweeps, double beta, double Delta, double V, double J,
                               double n, double *mu, double kappa, int obs_every,
