@@ -229,12 +229,20 @@ int ccmc_sync(ccmc_lattice *h);
  * The paper has no counterpart; it is a service of this library.
  *   d_state: Lx * Ly site codes (device memory, site (x, y) at y * Lx + x);
  *   d_out:   7 int64 in device memory, receives Nc, BV, BJ, M, M_stag, S_sum,
- *            S_stag exactly as ccmc_observables reports them.
+ *            S_stag of Eq. 3 by definition: the 2 Lx Ly right and down bonds
+ *            of the torus (on a 2-wide torus both bonds joining the same two
+ *            sites count), M_stag and S_stag with the sign of (x + y) mod 2.
+ *            For the shapes ccmc_lattice_create accepts these are exactly
+ *            what ccmc_observables reports; other shapes (odd sides, 2-wide
+ *            tori) are accepted too.
  * The reduction's scratch is a fixed static device array of 64 KB (1024 block
  * partials and a counter) that every GPU loading the library holds until exit;
  * lattices of any size up to Lx * Ly = 2^30 fit it (larger: E_INVAL), and
  * Lx, Ly >= 2.  The first call on a device looks up that array's address with
- * the device current; make that first call before any stream capture.  The work
+ * the device current and keeps it for the life of the process; make that
+ * first call before any stream capture, and do not call this function on a
+ * device after resetting it (cudaDeviceReset) in the same process: the kept
+ * address then belongs to the destroyed context.  The work
  * is queued on cuda_stream (NULL: the legacy default stream); synchronise before
  * reading d_out.  All calls share the one array, so calls that overlap on the
  * GPU (different streams, or another host thread) race and must not be issued.

@@ -50,6 +50,29 @@ def test_noalloc_recount_matches_observables_twice(shape):
                 assert list(got) == list(oracle.recount(lat.get_state()))
 
 
+@pytest.mark.parametrize("shape", [(2, 6), (5, 3), (7, 4), (2, 2), (3, 9)])
+def test_noalloc_recount_of_shapes_the_sweep_does_not_take(shape):
+    """Odd widths and 2-wide tori (which ccmc_lattice_create rejects) follow
+    Eq. 3 by definition: the 2N right and down bonds, both bonds counted where
+    a 2-wide torus joins the same two sites twice, the staggered sign (x + y)
+    mod 2 wrapping across an odd seam.  Compared with the oracle's recount of
+    uniformly random site codes, exactly, on two calls in a row."""
+    torch = pytest.importorskip("torch")
+    import paper_2301_11735_gb300 as cc
+
+    Lx, Ly = shape
+    fn = _fn(cc)
+    out = torch.zeros(7, dtype=torch.int64, device="cuda")
+    rng = np.random.default_rng(7 * Lx + Ly)
+    for call in range(2):
+        host = rng.integers(0, 4, size=(Ly, Lx), dtype=np.uint8)
+        st = torch.from_numpy(host.reshape(-1).copy()).cuda()
+        rc = fn(st.data_ptr(), Lx, Ly, out.data_ptr(), None)
+        assert rc == cc.OK, (call, rc)
+        torch.cuda.synchronize()
+        assert list(out.cpu().numpy()) == list(oracle.recount(host)), (call, shape)
+
+
 def test_noalloc_recount_rejects_bad_arguments():
     torch = pytest.importorskip("torch")
     import paper_2301_11735_gb300 as cc
