@@ -1,31 +1,39 @@
 """Benchmark of the coupled-pair Metropolis sweep on GB300.
 
-Workload (default): the 4096^2 temperature sweep -- four lattices of 4096 x 4096
-sites (Delta = 0, V = 0.5, J = 1, n = 0.1, charged fraction 0.3) at
-T = 0.2, 0.5, 1.0, 2.0, seeds 20..23.  One step = 10 sweeps of each of the
-four lattices (one ccmc_batch call; the four run concurrently on their own
-streams), plus the observable recount that closes every 10-sweep interval.  The metric is
-site-updates per second (one sweep = N site-updates).
+Workload (default, `large16384`): one 16384 x 16384 lattice near the
+charge-ordering crossover (Delta = 0.2, V = 1, J = 0.5, n = 0.05, charged
+fraction 0.3, T = 0.6, seed 5).  One step = 50 sweeps (one ccmc_batch_sweep
+call), with an exact recount of the observables and the histograms of M,
+M_stag and S_stag after every sweep.  `--workload temperature4096`: four
+4096 x 4096 lattices (Delta = 0, V = 0.5, J = 1, n = 0.1, T = 0.2, 0.5, 1, 2,
+seeds 20..23), one step = 200 sweeps of each (the four concurrently on their
+own streams), records every 10 sweeps.  The metric is site-updates per second
+(one sweep = N site-updates).
 
 Timing: W warm-up steps, then K timed steps, each bracketed by CUDA events on
-the issuing stream; L2 is flushed (a 256 MB write)
-between timed steps, outside the events.  nvidia-smi samples clocks during the
-timed region.  `e2e` repeats the steps through the C ABI with host buffers:
-every step uploads the lattices from pinned host memory in the compact form,
-2 bits a site (ccmc_set_state_packed, stream-ordered), and reads the
-observable records back (ccmc_obs_series).
+the issuing stream; L2 is flushed (a 256 MB write) between timed steps,
+outside the events.  nvidia-smi samples clocks during the timed region.
+`roofline` is the colour phase of the first lattice: 1.5 algorithmic bytes a
+site-update over its launch time, measured with CUDA events on the lattice's
+own stream around graphs of 128 phase launches, right after the timed steps
+(same lattice, stream and launch configuration); `roofline.aggregate` puts
+the same bytes over the whole timed run.  `e2e` repeats the steps through the
+C ABI with host buffers: every step uploads the lattices from pinned host
+memory in the compact form, 2 bits a site (ccmc_set_state_packed,
+stream-ordered), and reads the observable records back (ccmc_obs_series).
 
-Beside the headline the same JSON line carries more measurements: `paper_maps`
-(the paper's own host-built maps against the colour schedule), `batched` (512
-replicas of uneven L in one persistent launch, against back-to-back
-single-lattice launches), `served` (a Poisson request stream through the
+Beside the headline the same JSON line carries side measurements:
+`temperature4096` (the four 4096^2 lattices above, with their own roofline),
+`paper_maps` (the paper's own host-built maps against the colour schedule),
+`batched` (512 replicas of uneven L in one persistent launch, against the same
+lattices swept one at a time), `served` (a Poisson request stream through the
 continuous-batching server: p50/p99 latency, achieved vs offered
-site-updates/s, against back-to-back plain runs) and `small16` (the 16x16
-lattice's microseconds a sweep, plain and as a batch of one).
+site-updates/s, against the same requests run one at a time) and `small16`
+(the 16x16 lattice's microseconds a sweep, plain and as a batch of one).
 
 `--impl reference` times the CPU oracle (single-threaded C) on a bounded sample
-of the same workload.  Under torchrun each rank runs its own four lattices
-(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+of the same workload.  Under torchrun each rank runs its own lattices (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -49,7 +57,7 @@ STEP_SWEEPS = {"temperature4096": 200, "large16384": 50}
 OBS_EVERY = {"temperature4096": 10, "large16384": 1}
 
 # Counters of one phase launch of the bench's dominant kernel, from the ncu
-# captures summarised in profiles/phase_tile_kernel_<workload>.md:
+# captures of that kernel on each workload:
 # dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum.
 # They hold only for the kernel sources they were taken with (kernel_digest);
 # after any change to those sources the bench reports them as null.
@@ -315,21 +323,25 @@ def cpu_baseline_sample(sims, target_s: float = 12.0):
                       f"({dt:.1f} s, 1 thread)"}
 
 
-def measure_batched(cc, nsweeps=5000, plain_sample=32, plain_sweeps=200):
+def measure_batched(cc, nsweeps=5000, plain_per_size=4):
     """512 independent replicas (L in {32..256}, 5000 sweeps) in one batched
-    launch, against the same lattices swept back to back one at a time."""
+    call, against the same lattices swept one at a time: a stated subset
+    (the first `plain_per_size` lattices of every size), each for the full
+    5000 sweeps from the same state, whose final states must equal the
+    batch's bit for bit."""
+    import numpy as np
     import torch
 
     from workloads import replicas_512
 
     sims = replicas_512(nsweeps=nsweeps)
+    cols = ([s.beta for s in sims], [s.Delta for s in sims], [s.V for s in sims],
+            [s.J for s in sims])
     lats = []
     for s in sims:
         lat = cc.Lattice(s.Lx, s.Ly)
         lat.init_constrained(s.seed, s.n, s.charged_frac)
         lats.append(lat)
-    cols = ([s.beta for s in sims], [s.Delta for s in sims], [s.V for s in sims],
-            [s.J for s in sims])
     with cc.Batch(lats) as b:
         cfg = b.autotune(probe_sweeps=10)
         b.sweep(3, *cols)
@@ -340,13 +352,24 @@ def measure_batched(cc, nsweeps=5000, plain_sample=32, plain_sweeps=200):
         b.sync()
         dt = time.perf_counter() - t0
     work = sum(s.sites for s in sims) * nsweeps
-    sub = list(zip(sims, lats))[:plain_sample]
-    t0 = time.perf_counter()
-    for s, lat in sub:
-        lat.sweep(plain_sweeps, s.beta, s.Delta, s.V, s.J)
-        lat.sync()
-    dt_plain = time.perf_counter() - t0
-    plain = sum(s.sites for s, _ in sub) * plain_sweeps / dt_plain
+    picked, seen = [], {}
+    for i, s in enumerate(sims):
+        if seen.get(s.Lx, 0) < plain_per_size:
+            seen[s.Lx] = seen.get(s.Lx, 0) + 1
+            picked.append(i)
+    t_plain, identical = 0.0, True
+    for i in picked:
+        s = sims[i]
+        with cc.Lattice(s.Lx, s.Ly) as one:
+            one.init_constrained(s.seed, s.n, s.charged_frac)
+            one.sweep(3, s.beta, s.Delta, s.V, s.J)
+            one.sync()
+            t0 = time.perf_counter()
+            one.sweep(nsweeps, s.beta, s.Delta, s.V, s.J)
+            one.sync()
+            t_plain += time.perf_counter() - t0
+            identical &= bool(np.array_equal(one.get_state(), lats[i].get_state()))
+    plain = sum(sims[i].sites for i in picked) * nsweeps / t_plain
     for lat in lats:
         lat.close()
     return {"workload": "512 replicas, L~U{32,64,128,256}, T grid [0.1,3], n~U{0,.1,.2,.3}, "
@@ -354,8 +377,10 @@ def measure_batched(cc, nsweeps=5000, plain_sample=32, plain_sweeps=200):
             "value": work / dt, "unit": "site-updates/s", "seconds": dt,
             "config": {"threads": cfg[0], "resident_max_sites": cfg[1], "ctas_per_sm": cfg[2]},
             "plain_back_to_back": {"value": plain, "unit": "site-updates/s",
-                                   "sample": f"{plain_sample} of the lattices, {plain_sweeps} "
-                                             "sweeps each, one ccmc_sweep call at a time"},
+                                   "sample": f"{len(picked)} of the lattices ({plain_per_size} of "
+                                             f"each size), the full {nsweeps} sweeps each, one "
+                                             "ccmc_sweep call at a time",
+                                   "identical_final_states": identical},
             "speedup_vs_plain": (work / dt) / plain}
 
 
@@ -500,8 +525,150 @@ def measure_served(cc, count=120, plain_sample=24):
             "speedup_vs_plain": (work / span) / plain}
 
 
+def time_workload(cc, sims, step_sweeps, steps, warmup, dist, sampler=None, hist=False):
+    """Sweep `sims` (one lattice each, on their own streams, one ccmc_batch
+    call a step) for `warmup` untimed and `steps` timed steps of `step_sweeps`
+    sweeps, L2 flushed between timed steps; then time the colour phase of the
+    first lattice alone on its own stream, and repeat the steps end to end
+    from pinned host memory.  Returns the measured numbers."""
+    import torch
+
+    main = torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in sims]
+    lats = [cc.Lattice(s.Lx, s.Ly, stream=st) for s, st in zip(sims, streams)]
+    for lat, s in zip(lats, sims):
+        lat.init_constrained(s.seed, s.n, s.charged_frac)
+        if hist:
+            lat.hist_enable(1024)
+    batch = cc.Batch(lats, stream=main)
+    cols = ([s.beta for s in sims], [s.Delta for s in sims], [s.V for s in sims],
+            [s.J for s in sims])
+    obs_every = sims[0].obs_every
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(main)
+        for st in streams:
+            st.wait_event(ev0)
+        batch.sweep(step_sweeps, *cols, obs_every=obs_every)
+        for st in streams:
+            e = torch.cuda.Event()
+            e.record(st)
+            main.wait_event(e)
+        ev1.record(main)
+        return ev0, ev1
+
+    evs = []
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark(0)
+    t_wall = time.perf_counter()
+    for _ in range(steps):
+        with torch.cuda.stream(main):
+            flush.zero_()
+        evs.append(step())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if sampler:
+        sampler.mark(1)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
+    updates_per_step = sum(s.sites for s in sims) * step_sweeps
+    world = dist.get_world_size() if dist else 1
+    value = updates_per_step * steps * world / total_s
+
+    # the dominant kernel: the colour phase of the first lattice, in the launch
+    # configuration of the timed steps (same lattice, stream and graphs).  A
+    # chunk of 16 sweeps is 128 phase launches (plus a one-thread counter
+    # advance), replayed as one graph; events on the lattice's stream around it
+    # give the average phase-launch time (slightly over, by the advance).
+    lat0, s0, st0 = lats[0], sims[0], streams[0]
+    cal = []
+    for _ in range(6):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st0)
+        lat0.sweep(16, s0.beta, s0.Delta, s0.V, s0.J, obs_every=0)
+        b.record(st0)
+        cal.append((a, b))
+    torch.cuda.synchronize()
+    phase_ms = statistics.mean(x.elapsed_time(y) for x, y in cal[2:]) / 128
+
+    # end to end through the C ABI with host buffers: every step uploads each
+    # lattice's state in the compact form (2 bits a site) from pinned host
+    # memory, stream-ordered so that one lattice's upload overlaps the others'
+    # sweeps, and reads the records back
+    recs_per_step = step_sweeps // obs_every if obs_every > 0 else 0
+    host_states = [torch.from_numpy(lat.get_state_packed()).pin_memory() for lat in lats]
+    rec_bytes = 0
+    e2e_times = []
+    for k in range(max(2, steps // 2) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for lat, s, h in zip(lats, sims, host_states):
+            lat.set_state_packed_ptr(h.data_ptr(), s.seed, 0)
+        batch.sweep(step_sweeps, *cols, obs_every=obs_every)
+        recs = [lat.obs_series(cap=max(recs_per_step, 1)) for lat in lats]
+        dt = time.perf_counter() - t0
+        rec_bytes = sum(r.nbytes for r in recs)
+        if k > 0:
+            e2e_times.append(dt)
+    e2e_value = updates_per_step * len(e2e_times) * world / max_over_ranks(sum(e2e_times), dist,
+                                                                           "cuda")
+    batch.close()
+    for lat in lats:
+        lat.close()
+    del flush
+    return {"value": value, "total_s": total_s, "step_ms": step_ms, "t_wall": t_wall,
+            "phase_ms": phase_ms, "e2e_value": e2e_value,
+            "h2d": int(sum(h.numel() for h in host_states)), "d2h": int(rec_bytes)}
+
+
+def roofline(name, s0, m, value, peak, peak_kind, clocks, local):
+    """The roofline object of the colour phase of lattice s0: algorithmic bytes
+    (1.5 B a site-update, N/8 updates a phase launch) over the measured launch
+    time; `aggregate` carries the same bytes over the whole timed run."""
+    import torch
+
+    alg_bytes = 1.5 * s0.sites / 8
+    achieved = alg_bytes / (m["phase_ms"] * 1e-3) / 1e9
+    counters = PHASE_COUNTERS.get(name)
+    if counters and counters["digest"] != kernel_digest():
+        counters = None  # the kernel changed since the capture
+    issue = None
+    if counters:
+        # warp-instructions per second against one per scheduler per cycle
+        # (4 schedulers per SM) at the maximum SM clock
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_issue = 4 * sms * float((clocks or {}).get("sm_max_mhz") or 2070.0) * 1e6
+        rate = counters["warp_inst"] / (m["phase_ms"] * 1e-3)
+        issue = {"warp_inst_per_launch": counters["warp_inst"], "achieved": rate,
+                 "peak": peak_issue, "unit": "warp-inst/s", "frac": rate / peak_issue}
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": counters["traffic"] if counters else None,
+            "issue": issue,
+            "limiter": PHASE_LIMITER.get(name) if counters else None,
+            "kernel": f"colour phase of one {s0.Lx}^2 lattice "
+                      f"({tile_kernel_name(s0) if tile_ok(s0) else 'phase_kernel'})",
+            "peak_source": peak_kind, "launch_ms": m["phase_ms"],
+            # the same algorithmic bytes over the whole timed run (every lattice's
+            # phases, recounts and histograms included)
+            "aggregate": {"achieved": 1.5 * value / 1e9, "frac": 1.5 * value / 1e9 / peak,
+                          "unit": "GB/s"}}
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
     import paper_2301_11735_gb300 as cc
@@ -518,161 +685,64 @@ def run_ours(args):
     step_sweeps = args.sweeps_per_step or STEP_SWEEPS[args.workload]
     if step_sweeps % sims[0].obs_every:
         raise SystemExit(f"--sweeps-per-step must be a multiple of {sims[0].obs_every}")
-    recs_per_step = step_sweeps // sims[0].obs_every
-    # explicit streams: one issuing stream for the timing events and the L2 flush,
-    # one per lattice so that the four run concurrently (torch's default stream
-    # has handle 0, which the library reads as "create your own")
-    main = torch.cuda.Stream()
-    streams = [torch.cuda.Stream() for _ in sims]
-    lats = [cc.Lattice(s.Lx, s.Ly, stream=st) for s, st in zip(sims, streams)]
-    for lat, s in zip(lats, sims):
-        lat.init_constrained(s.seed, s.n, s.charged_frac)
-        if args.workload == "large16384":
-            lat.hist_enable(1024)
-    batch = cc.Batch(lats, stream=main)
-    cols = ([s.beta for s in sims], [s.Delta for s in sims], [s.V for s in sims],
-            [s.J for s in sims])
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
-
-    def step():
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(main)
-        for st in streams:
-            st.wait_event(ev0)
-        batch.sweep(step_sweeps, *cols, obs_every=sims[0].obs_every)
-        for st in streams:
-            e = torch.cuda.Event()
-            e.record(st)
-            main.wait_event(e)
-        ev1.record(main)
-        return ev0, ev1
-
     sampler = ClockSampler(local)
-    evs = []
     with sampler:
-        for _ in range(args.warmup):
-            step()
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        sampler.mark(0)
-        t_wall = time.perf_counter()
-        for _ in range(args.steps):
-            with torch.cuda.stream(main):
-                flush.zero_()
-            evs.append(step())
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall
-        sampler.mark(1)
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
+        m = time_workload(cc, sims, step_sweeps, args.steps, args.warmup, dist, sampler,
+                          hist=args.workload == "large16384")
     clocks = sampler.summary()
-    updates_per_step = sum(s.sites for s in sims) * step_sweeps
-    value = updates_per_step * args.steps * world / total_s
-
-    # dominant kernel: the colour phase of one 4096^2 lattice.  A chunk of 16
-    # sweeps is 128 phase launches (plus a one-thread counter advance), replayed
-    # as one graph; events on the lattice's stream around it give the average
-    # phase-launch time (slightly over, by the advance).
-    lat0, s0, st0 = lats[0], sims[0], streams[0]
-    cal = []
-    for _ in range(6):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(st0)
-        lat0.sweep(16, s0.beta, s0.Delta, s0.V, s0.J, obs_every=0)
-        b.record(st0)
-        cal.append((a, b))
-    torch.cuda.synchronize()
-    phase_ms = statistics.mean(x.elapsed_time(y) for x, y in cal[2:]) / 128
-    # 1.5 B per site-update, N/8 updates per phase
-    alg_bytes = 1.5 * s0.sites / 8
+    value = m["value"]
     peak, peak_kind = _peaks()
-    achieved = alg_bytes / (phase_ms * 1e-3) / 1e9
-    counters = PHASE_COUNTERS.get(args.workload)
-    if counters and counters["digest"] != kernel_digest():
-        counters = None  # the kernel changed since the capture
-    issue = None
-    if counters:
-        # warp-instructions per second against one per scheduler per cycle
-        # (4 schedulers per SM) at the maximum SM clock
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        peak_issue = 4 * sms * float(clocks.get("sm_max_mhz") or 2070.0) * 1e6
-        rate = counters["warp_inst"] / (phase_ms * 1e-3)
-        issue = {"warp_inst_per_launch": counters["warp_inst"], "achieved": rate,
-                 "peak": peak_issue, "unit": "warp-inst/s", "frac": rate / peak_issue}
-
-    # end to end through the C ABI with host buffers: every step uploads each
-    # lattice's state in the compact form (2 bits a site) from pinned host
-    # memory, stream-ordered so that one lattice's upload overlaps the others'
-    # sweeps, and reads the records back
-    host_states = []
-    for lat in lats:
-        h = torch.from_numpy(lat.get_state_packed()).pin_memory()
-        host_states.append(h)
-    rec_bytes = 0
-    e2e_times = []
-    for k in range(max(2, args.steps // 2) + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for lat, s, h in zip(lats, sims, host_states):
-            lat.set_state_packed_ptr(h.data_ptr(), s.seed, 0)
-        batch.sweep(step_sweeps, *cols, obs_every=sims[0].obs_every)
-        recs = [lat.obs_series(cap=recs_per_step) for lat in lats]
-        dt = time.perf_counter() - t0
-        rec_bytes = sum(r.nbytes for r in recs)
-        if k > 0:
-            e2e_times.append(dt)
-    e2e_value = updates_per_step * len(e2e_times) * world / max_over_ranks(sum(e2e_times), dist,
-                                                                           "cuda")
 
     if rank == 0:
+        s0 = sims[0]
         line = {
             "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "ms_per_step": 1e3 * m["total_s"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": workload_desc,
                        "lattices_per_gpu": len(sims), "sweeps_per_step": step_sweeps,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
-            "clocks": clocks, "wall_s": t_wall,
+            "clocks": clocks, "wall_s": m["t_wall"],
             # per step and lattice: 8 phase launches a sweep, the recounts, counter advances
             "gpu_launches": args.steps * len(sims) * launches_per_call(
-                step_sweeps, sims[0].obs_every, step_sweeps),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": counters["traffic"] if counters else None,
-                         "issue": issue,
-                         "limiter": PHASE_LIMITER.get(args.workload) if counters else None,
-                         "kernel": f"colour phase of one {s0.Lx}^2 lattice "
-                                   f"({tile_kernel_name(s0) if tile_ok(s0) else 'phase_kernel'})",
-                         "peak_source": peak_kind, "launch_ms": phase_ms,
-                         # the same algorithmic bytes over the whole timed region, every
-                         # lattice's phases together (they overlap on their own streams)
-                         "aggregate": {"achieved": 1.5 * value / 1e9, "frac": 1.5 * value / 1e9 / peak,
-                                       "unit": "GB/s"}},
-            "e2e": {"value": e2e_value, "unit": "site-updates/s",
-                    "h2d_bytes_per_step": int(sum(h.numel() for h in host_states)),
-                    "d2h_bytes_per_step": int(rec_bytes)},
+                step_sweeps, s0.obs_every, step_sweeps),
+            "roofline": roofline(args.workload, s0, m, value, peak, peak_kind, clocks, local),
+            "e2e": {"value": m["e2e_value"], "unit": "site-updates/s",
+                    "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"]},
         }
-        if not args.no_side and args.workload == "temperature4096":
+        # share of the timed steps spent in phase launches (the rest: recounts,
+        # histograms, counter advances)
+        line["roofline"]["phase_share"] = (8 * step_sweeps * len(sims) * m["phase_ms"]
+                                           / (1e3 * m["total_s"] / args.steps))
+        if not args.no_side:
+            if args.workload == "large16384":
+                line["temperature4096"] = measure_temperature(cc, args, peak, peak_kind, local)
             line["batched"] = measure_batched(cc)
-            line["served"] = measure_served(cc)
+            line["served"] = measure_served(cc, count=args.served_requests)
             line["paper_maps"] = measure_paper_maps(cc)
             line["small16"] = measure_small(cc)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample(sims)
         print(json.dumps(line), flush=True)
-    batch.close()
-    for lat in lats:
-        lat.close()
     if dist:
         dist.destroy_process_group()
+
+
+def measure_temperature(cc, args, peak, peak_kind, local):
+    """Side measurement: the 4096^2 temperature sweep (four lattices on their
+    own streams, 200 sweeps each a step, records every 10 sweeps), 10 timed
+    steps after 3 warm-up steps, with its own roofline object."""
+    sims, desc = workload("temperature4096")
+    step_sweeps = STEP_SWEEPS["temperature4096"]
+    m = time_workload(cc, sims, step_sweeps, 10, 3, None)
+    out = {"workload": desc, "value": m["value"], "unit": "site-updates/s",
+           "ms_per_step": 1e3 * m["total_s"] / 10, "steps": 10, "warmup": 3,
+           "e2e": {"value": m["e2e_value"], "unit": "site-updates/s",
+                   "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"]},
+           "roofline": roofline("temperature4096", sims[0], m, m["value"], peak, peak_kind,
+                                None, local)}
+    return out
 
 
 def main():
@@ -686,10 +756,12 @@ def main():
                     help="skip the batched-replica and served-stream measurements")
     ap.add_argument("--sweeps-per-step", type=int, default=0,
                     help="sweeps of every lattice per step (default: the workload's)")
-    ap.add_argument("--workload", default="temperature4096",
+    ap.add_argument("--workload", default="large16384",
                     choices=["temperature4096", "large16384"],
-                    help="temperature4096 (default): four 4096^2 lattices; large16384: one "
-                         "16384^2 lattice with observables and histograms every sweep")
+                    help="large16384 (default): one 16384^2 lattice with observables and "
+                         "histograms every sweep; temperature4096: four 4096^2 lattices")
+    ap.add_argument("--served-requests", type=int, default=2000,
+                    help="requests of the served Poisson stream (side measurement)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
