@@ -29,6 +29,8 @@ enum CtlSlot : int {
   kCtlTicket = 2,     // arrival counter of the recount's last-block reduction
   kCtlStatus = 3,     // device-side error flag
   kCtlLatest = 4,     // 8 words: the last recount record
+  kCtlTileClaim = 12,  // 2 words: tile claims of the tile-staged phases of even
+                       // and odd P (phase P's low 32 bits above the claim count)
   kCtlWords = 16
 };
 

@@ -387,29 +387,42 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *th
 // ----------------------------------------------------------------------------
 // Tile-staged phase (lattices whose class rows are W words with W dividing 256
 // and a multiple of 4, and Cy a multiple of R = 256 / W).  A tile is R
-// consecutive rows of the a-class (256 words, one per thread); CTA c takes
-// tiles c, c + grid, c + 2 grid, ...  (Handing out tiles by an atomic counter
-// measured slower: the claim's latency lands on the staging thread.)  Thread 0
-// stages a tile's ten row bands -- the a rows, the b rows and the rows of all eight
-// neighbour classes, each band R full rows -- into shared memory with bulk
-// asynchronous copies that complete on the buffer's `full` mbarrier; the
-// threads evaluate their words from shared memory; each warp then arrives on
-// the buffer's `done` mbarrier and goes on to the next tile without waiting for
-// the other warps.  One tile later thread 0 waits for `done`, sends the tile's
-// a and b bands back with bulk copies, and stages the next tile into the buffer
-// whose write-back has finished reading it.  Three buffers rotate: tile k is
-// evaluated while tile k - 1 goes back and tile k + 1 arrives.  (Waiting for
-// `done` right after its own word, to stage two tiles ahead, measured slower:
-// thread 0's warp then trails the slowest warp every tile.)  No two tiles of
-// a phase write the same rows (each b row is the partner row of exactly one a
-// row), and no tile reads a row another tile writes (the pairs of a phase do
-// not interact), so global memory sees no atomics and staging may run ahead of
-// the write-back.
+// consecutive rows of the a-class (256 words, one per thread).  CTA c takes
+// tiles c, c + grid, ... c + (kBufs - 1) grid first, then claims tiles beyond
+// kBufs grid one at a time from a counter in the lattice's control block, so
+// that CTAs which start late (placed on an SM whose previous CTA finished
+// last) take fewer tiles instead of ending the phase late.  The claim for a
+// buffer is made when the buffer is refilled, kBufs - 1 tiles ahead of its
+// use, so its latency is hidden.  Phase P claims from slot P mod 2; its kernel
+// tags slot (P + 1) mod 2 for phase P + 1 (with P + 1 in the high word) once
+// phase P - 1 is done with it; a slot whose tag is not the phase's own (the
+// previous phase ran on another path, or the phase counter was just set: that
+// zeroes both slots) makes every CTA of the phase keep to the fixed order c +
+// t grid.  A tile's ten row bands -- the a rows,
+// the b rows and the rows of all eight neighbour classes, each band R full
+// rows -- arrive in shared memory by bulk asynchronous copies (one band per
+// lane of the staging warp) that complete on the buffer's `full` mbarrier.
+// The threads evaluate their words from shared memory.  The last warp to
+// finish a tile (counted on the buffer's arrival counter) sends its a and b
+// bands back to global memory with plain vector stores and stages the tile
+// kBufs later into the same buffer, so every buffer is refilled as soon as it
+// is free, kBufs - 1 tiles ahead of its use, and no warp waits for another
+// warp except on a tile's data.  (A fixed staging thread that first evaluated
+// its own word trailed the slowest warp every tile; the other warps' polls
+// then starved it of issue slots: first tiles landed 2.6 to 19 us after a
+// phase started.)  Waits suspend in hardware (try_wait with a time hint)
+// instead of spinning.  No two tiles of a phase write the same rows (each b
+// row is the partner row of exactly one a row), and no tile reads a row
+// another tile writes (the pairs of a phase do not interact), so global memory
+// sees no atomics and staging may run ahead of the write-back.
 constexpr int kTileWords = 256;
 constexpr int kBands = 10;
 constexpr int kTileBufs = 3;
 constexpr int kTileWarps = kTileWords / 32;
-constexpr int kWaitSpins = 1 << 20;  // bounded mbarrier waits
+constexpr uint32_t kTileBytes = kBands * kTileWords * 4;
+constexpr uint32_t kWaitSpins = 1u << 24;              // bounded mbarrier waits:
+constexpr unsigned long long kWaitNs = 1000000000ull;  // at most 2^24 polls or 1 s
+constexpr uint32_t kSuspendNs = 20000;                 // suspend-time hint of a poll
 
 // The lattice's threshold tops and the move table, contiguous in device
 // memory (thrhi, trans -- or the compact copy thrhi16, trans16), staged with
@@ -422,6 +435,13 @@ struct TileTables {
   static_assert(kBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
 
+// Row band: R rows of one class starting at row j0 + dy of the tile's first a
+// row j0 (periodic in Cy).
+struct Band {
+  const uint32_t *cls;
+  int dy;
+};
+
 // kBufs: band buffers (three for the pipelined tile loop, one for a CTA that
 // takes a single tile).
 template <class ThrT, int kBufs = kTileBufs>
@@ -430,30 +450,48 @@ struct TileSmem {
   uint2 trans[kMoveN];  // directly after thrhi, as in device memory
   alignas(128) uint32_t band[kBufs][kBands][kTileWords];
   alignas(8) unsigned long long full[kBufs];  // bands landed (transaction count)
-  alignas(8) unsigned long long done[kBufs];  // every warp finished the tile
-  alignas(8) unsigned long long tables;           // the tables landed
+  alignas(8) unsigned long long tables;       // the tables landed
+  int done[kBufs];     // warps finished with the buffer's tile
+  int armed[kBufs];    // times the buffer's `full` barrier was armed
+  int tile[kBufs];     // the tile staged in the buffer, -1: no more tiles
+  Band bands[kBands];
   Sched sched;
   int err;
   int busy0, busy1;  // classes the previous phase writes (early staging waits for them)
-  unsigned staged;  // thread 0: buffers whose bulk loads it has not waited for
-  unsigned dpar;    // thread 0, bit b: parity of the phase of done[b] waited for next
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase of parity `parity` of the mbarrier at `bar` to complete:
+// true when it did, false after kWaitSpins polls or kWaitNs nanoseconds.  Each
+// poll may suspend the thread (up to kSuspendNs) until the phase completes.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int i = 0; i < kWaitSpins; ++i) {
+  unsigned long long t0 = 0;
+  for (uint32_t i = 0; i < kWaitSpins; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (ok) return true;
+    if ((i & 63u) == 0) {
+      const unsigned long long t = global_ns();
+      if (i == 0)
+        t0 = t;
+      else if (t - t0 > kWaitNs)
+        return false;
+    }
   }
   return false;
 }
@@ -467,18 +505,10 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
       : "memory");
 }
 
-__device__ __forceinline__ void bulk_store(void *dst, uint32_t src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
-               :
-               : "l"(dst), "r"(src), "r"(bytes)
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
-
-// Row band: R rows of one class starting at row r0 (periodic in Cy).
-struct Band {
-  const uint32_t *cls;
-  int dy;  // first row relative to the tile's first a row
-};
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -486,8 +516,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 
 // One tile-staged phase of lattice g by CTA `cta` of the `ncta` CTAs that
 // work on it; keys: the source of its Philox keys.
-// kSingle: every CTA takes exactly one tile (ncta == tiles): one band buffer,
-// no pipeline.
+// kSingle: every CTA takes at most one tile (ncta == tiles): one band buffer.
 template <class ThrT, bool kSingle, class Keys>
 __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
                                            const uint32_t *thr32, int64_t p_off, int cta,
@@ -499,28 +528,27 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
   Smem &sm = *reinterpret_cast<Smem *>(tile_smem);
   static_assert(offsetof(Smem, trans) == sizeof(ThrT) * TileTables<ThrT>::kTops,
                 "tables staged as one block");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     sm.err = 0;
     for (int b = 0; b < kBufs; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.full[b])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.done[b])),
-                   "r"(kTileWarps));
+      sm.done[b] = 0;
+      sm.armed[b] = 0;
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.tables)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // The tables come from host uploads that precede the whole launch chain:
     // their copy may start before the previous kernel of the stream finishes.
     const uint32_t bar = smem_u32(&sm.tables);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"(kStagedTableBytes)
-                 : "memory");
+    mbar_expect(bar, kStagedTableBytes);
     bulk_load(smem_u32(sm.thrhi), thrhi, kStagedTableBytes, bar);
   }
   // The phase index.  A launch after the first of a chain (p_off > 0) reads the
   // counter base before it waits for its predecessor: the base was written by
   // a kernel at least two launches back (the chain's counter advance), which
   // the predecessor's griddepcontrol.wait has already waited for.  It then
-  // stages the bands of its first tile that lie in classes the predecessor
+  // stages the bands of its first tiles that lie in classes the predecessor
   // (phase P - 1, whose schedule it draws too) does not write, while that
   // phase is still finishing, and the other bands once it has finished.  Only
   // lattices whose phases give every CTA several tiles do this: for smaller ones
@@ -531,15 +559,23 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
     asm volatile("griddepcontrol.launch_dependents;");
   }
   const uint64_t P = (uint64_t)(g.ctl[kCtlPhaseBase] + p_off);
-  if (threadIdx.x < 32) {
+  if (warp == 0) {
     const Sched sc = draw_schedule(g, P);
-    if (threadIdx.x == 0) sm.sched = sc;
     if (early) {
       const Sched pv = draw_schedule(g, P - 1u);
-      if (threadIdx.x == 0) {
+      if (lane == 0) {
         sm.busy0 = pv.a0y * 4 + pv.a0x;
         sm.busy1 = ((pv.a0y + pv.ry) & 3) * 4 + ((pv.a0x + pv.rx) & 3);
       }
+    }
+    if (lane == 0) {
+      sm.sched = sc;
+      const PhaseU u0 = phase_uniform(g, sc);
+      const Band bs[kBands] = {{u0.cA, 0},       {u0.cAL, 0},       {u0.cAR, 0},
+                               {u0.cAU, u0.dyAU}, {u0.cAD, u0.dyAD}, {u0.cB, u0.qy},
+                               {u0.cBL, u0.qy},   {u0.cBR, u0.qy},   {u0.cBU, u0.qy + u0.dyBU},
+                               {u0.cBD, u0.qy + u0.dyBD}};
+      for (int k = 0; k < kBands; ++k) sm.bands[k] = bs[k];
     }
   }
   __syncthreads();
@@ -547,83 +583,74 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
   const uint32_t near128 = sc.near ? 128u : 0u;
   const PhaseU u = phase_uniform(g, sc);
   const int W = g.W, R = kTileWords / W, Cy = g.Cy;
-  const Band bands[kBands] = {{u.cA, 0},          {u.cAL, 0},          {u.cAR, 0},
-                              {u.cAU, u.dyAU},    {u.cAD, u.dyAD},     {u.cB, u.qy},
-                              {u.cBL, u.qy},      {u.cBR, u.qy},       {u.cBU, u.qy + u.dyBU},
-                              {u.cBD, u.qy + u.dyBD}};
   const int ntiles = Cy / R;
   const uint32_t row_bytes = (uint32_t)W * 4u;
-  // row r (in [-Cy, 2 Cy)) of a class, periodic
-  auto wrap_row = [&](int r) { return r < 0 ? r + Cy : (r >= Cy ? r - Cy : r); };
 
-  // thread 0: the bands of tile `tile` selected by `mask` into buffer `buf`
-  auto stage_bands = [&](int tile, int buf, unsigned mask) {
-    const uint32_t bar = smem_u32(&sm.full[buf]);
-    const int j0 = tile * R;
-    for (int k = 0; k < kBands; ++k) {
-      if (!(mask & (1u << k))) continue;
-      const int r0 = wrap_row(wrap_row(j0 + bands[k].dy));
+  // lane `lane` (< kBands) of the calling warp: the bulk loads of band `lane`
+  // of tile `tile` into buffer b, if `mask` selects it
+  auto stage_band = [&](int tile, int b, unsigned mask) {
+    if (lane < kBands && ((mask >> lane) & 1u)) {
+      const Band bd = sm.bands[lane];
+      const int j0 = tile * R;
+      int r0 = j0 + bd.dy;  // in [-Cy, 2 Cy)
+      r0 = r0 < 0 ? r0 + Cy : (r0 >= Cy ? r0 - Cy : r0);
       const int n1 = min(R, Cy - r0);
-      const uint32_t dst = smem_u32(&sm.band[buf][k][0]);
-      bulk_load(dst, bands[k].cls + (int64_t)r0 * W, (uint32_t)n1 * row_bytes, bar);
-      if (n1 < R) bulk_load(dst + (uint32_t)n1 * row_bytes, bands[k].cls, (uint32_t)(R - n1) * row_bytes, bar);
+      const uint32_t bar = smem_u32(&sm.full[b]);
+      const uint32_t dst = smem_u32(&sm.band[b][lane][0]);
+      bulk_load(dst, bd.cls + (int64_t)r0 * W, (uint32_t)n1 * row_bytes, bar);
+      if (n1 < R)
+        bulk_load(dst + (uint32_t)n1 * row_bytes, bd.cls, (uint32_t)(R - n1) * row_bytes, bar);
     }
   };
-  auto expect_tile = [&](int buf) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                     smem_u32(&sm.full[buf])),
-                 "r"((uint32_t)(kBands * kTileWords * 4))
-                 : "memory");
+  // lane 0 of the calling warp arms buffer b for tile `tile` (its ten bands'
+  // bytes), or marks it empty (tile < 0: the barrier completes at once)
+  auto arm = [&](int tile, int b) {
+    if (lane == 0) {
+      ++sm.armed[b];
+      sm.tile[b] = tile;
+      if (tile >= 0)
+        mbar_expect(smem_u32(&sm.full[b]), kTileBytes);
+      else
+        mbar_arrive(smem_u32(&sm.full[b]));
+    }
+    __syncwarp();
   };
-  // thread 0 stages tile `tile` into buffer `buf`
-  auto stage = [&](int tile, int buf) {
-    expect_tile(buf);
-    stage_bands(tile, buf, (1u << kBands) - 1u);
-  };
-  // thread 0 sends the a and b bands of tile `tile` (buffer `buf`) back
-  auto write_back = [&](int tile, int buf) {
-    const int j0 = tile * R;
-    bulk_store(const_cast<uint32_t *>(u.cA) + (int64_t)j0 * W, smem_u32(&sm.band[buf][0][0]),
-               (uint32_t)R * row_bytes);
-    const int rb = wrap_row(j0 + u.qy);
-    const int n1 = min(R, Cy - rb);
-    const uint32_t src = smem_u32(&sm.band[buf][5][0]);
-    bulk_store(const_cast<uint32_t *>(u.cB) + (int64_t)rb * W, src, (uint32_t)n1 * row_bytes);
-    if (n1 < R)
-      bulk_store(const_cast<uint32_t *>(u.cB), src + (uint32_t)n1 * row_bytes,
-                 (uint32_t)(R - n1) * row_bytes);
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-  };
-
+  // the first kBufs tiles are fixed (cta + i ncta), staged by warp 0
+  auto first_tile = [&](int i) { return cta + i * ncta < ntiles ? cta + i * ncta : -1; };
   if (early) {
     unsigned busy = 0u;  // bands in the classes the previous phase writes
     for (int k = 0; k < kBands; ++k)
-      if (bands[k].cls == g.words + (int64_t)sm.busy0 * g.cstride ||
-          bands[k].cls == g.words + (int64_t)sm.busy1 * g.cstride)
+      if (sm.bands[k].cls == g.words + (int64_t)sm.busy0 * g.cstride ||
+          sm.bands[k].cls == g.words + (int64_t)sm.busy1 * g.cstride)
         busy |= 1u << k;
-    if (threadIdx.x == 0 && cta < ntiles) {
-      expect_tile(0);
-      stage_bands(cta, 0, ~busy & ((1u << kBands) - 1u));
+    if (warp == 0) {
+      for (int i = 0; i < kBufs; ++i) {
+        arm(first_tile(i), i);
+        if (first_tile(i) >= 0) stage_band(first_tile(i), i, ~busy & ((1u << kBands) - 1u));
+      }
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    if (threadIdx.x == 0 && cta < ntiles) stage_bands(cta, 0, busy);
-  } else if (threadIdx.x == 0 && cta < ntiles) {
-    stage(cta, 0);
+    if (warp == 0)
+      for (int i = 0; i < kBufs; ++i)
+        if (first_tile(i) >= 0) stage_band(first_tile(i), i, busy);
+  } else if (warp == 0) {
+    for (int i = 0; i < kBufs; ++i) {
+      arm(first_tile(i), i);
+      if (first_tile(i) >= 0) stage_band(first_tile(i), i, (1u << kBands) - 1u);
+    }
   }
-  if (threadIdx.x == 0) {
-    sm.staged = cta < ntiles ? 1u : 0u;
-    sm.dpar = 0u;
-  }
-  __syncthreads();  // the mbarrier initialisation
+  // phase P - 1 is done (griddepcontrol.wait): tag the claim slot of phase P + 1
+  if (!kSingle && cta == 0 && threadIdx.x == 0)
+    *reinterpret_cast<volatile unsigned long long *>(g.ctl + kCtlTileClaim + ((P + 1u) & 1u)) =
+        (unsigned long long)(uint32_t)(P + 1u) << 32;
   if (!mbar_wait(smem_u32(&sm.tables), 0u)) sm.err = 1;
 
   const int lw = __ffs(W) - 1;  // W is a power of two
   const int jr = threadIdx.x >> lw, w = threadIdx.x & (W - 1);
-  const bool lane0 = (threadIdx.x & 31) == 0;
-  // a tile's bands from buffer buf as the windows' sources
-  auto local_u = [&](int buf) {
-    const uint32_t *base = sm.band[buf][0];
+  // a tile's bands in buffer b as the windows' sources
+  auto local_u = [&](int b) {
+    const uint32_t *base = sm.band[b][0];
     PhaseU lu = u;
     lu.cA = base;
     lu.cAL = base + 1 * kTileWords;
@@ -637,99 +664,80 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
     lu.cBD = base + 9 * kTileWords;
     return lu;
   };
-  if constexpr (kSingle) {
-    // one tile: evaluate it, then thread 0 sends its a and b bands back
-    if (cta < ntiles) {
-      if (mbar_wait(smem_u32(&sm.full[0]), 0u)) {
-        if (threadIdx.x == 0) sm.staged = 0u;
-        phase_word<kRowTile>(g, local_u(0), sm.trans, sm.thrhi, thr32, cta * R + jr, jr, w, P,
-                             near128, keys);
-      } else {
-        sm.err = 1;
-      }
+  int b = 0;
+  for (int t = 0;; ++t) {
+    // (1) evaluate this thread's word of the tile in buffer b, if any
+    if (!mbar_wait(smem_u32(&sm.full[b]), (uint32_t)(t / kBufs) & 1u)) {
+      sm.err = 1;
+      break;
     }
+    const int tile = sm.tile[b];
+    if (tile < 0) break;
+    phase_word<kRowTile>(g, local_u(b), sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P,
+                         near128, keys);
+    // (2) this warp is done with the tile: its shared-memory writes are ordered
+    // before the async copies that will refill the buffer, and before the
+    // last warp's reads
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
-    if (lane0) mbar_arrive(smem_u32(&sm.done[0]));
-    if (threadIdx.x == 0) {
-      if (cta < ntiles && !sm.err) {
-        if (mbar_wait(smem_u32(&sm.done[0]), 0u))
-          write_back(cta, 0);
-        else
-          sm.err = 1;
-      }
-      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-      if (sm.err) {
-        // give loads still in flight a bounded chance to land before exiting
-        mbar_wait(smem_u32(&sm.tables), 0u);
-        if (sm.staged & 1u) mbar_wait(smem_u32(&sm.full[0]), 0u);
-        g.ctl[kCtlStatus] = 1;
-      }
+    int last = 0;
+    if (lane == 0) {
+      __threadfence_block();
+      last = atomicAdd(&sm.done[b], 1) == kTileWarps - 1;
+      if (last) __threadfence_block();
     }
-    return;
-  }
-  uint32_t fpar = 0u;  // bit b: parity of the phase of full[b] waited for next
-  int buf = 0, k = 0;
-  int tile = cta;
-  for (; tile < ntiles; tile += ncta, ++k) {
-    if (threadIdx.x == 0) {
-      // (1) stage the next tile into the buffer of tile k - 2, whose
-      // write-back (issued one tile ago, the only copies outstanding) must
-      // have finished reading it
-      const int next = tile + ncta;
-      if (next < ntiles) {
-        const int nb = buf == kTileBufs - 1 ? 0 : buf + 1;
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-        stage(next, nb);
-        sm.staged |= 1u << nb;
-      }
-      // (2) send tile k - 1 back once every warp is done with it
-      if (k >= 1) {
-        const int pb = buf == 0 ? kTileBufs - 1 : buf - 1;
-        if (mbar_wait(smem_u32(&sm.done[pb]), (sm.dpar >> pb) & 1u)) {
-          sm.dpar ^= 1u << pb;
-          write_back(tile - ncta, pb);
-        } else {
-          sm.err = 1;
+    last = __shfl_sync(0xFFFFFFFFu, last, 0);
+    __syncwarp();
+    if (last) {
+      // (3) the last warp: write the a and b bands back, then refill the buffer
+      if (*(volatile int *)&sm.err == 0) {
+        const int j0 = tile * R;
+        const uint4 *sa = reinterpret_cast<const uint4 *>(sm.band[b][0]);
+        const uint4 *sb = reinterpret_cast<const uint4 *>(sm.band[b][5]);
+        uint4 *ga = reinterpret_cast<uint4 *>(const_cast<uint32_t *>(u.cA) + (int64_t)j0 * W);
+        int rb = j0 + u.qy;
+        rb = rb >= Cy ? rb - Cy : rb;
+        const int split = min(R, Cy - rb) * W / 4;  // uint4 before the band wraps
+        uint4 *gb = reinterpret_cast<uint4 *>(const_cast<uint32_t *>(u.cB));
+        const int64_t gb1 = (int64_t)rb * W / 4;  // in uint4
+#pragma unroll
+        for (int q = lane; q < kTileWords / 4; q += 32) {
+          ga[q] = sa[q];
+          gb[q < split ? gb1 + q : (int64_t)(q - split)] = sb[q];
         }
       }
+      __syncwarp();
+      if constexpr (!kSingle) {
+        // the buffer's next tile: claimed, or in the fixed order when the
+        // claim slot is not this phase's
+        int next = 0;
+        if (lane == 0) {
+          sm.done[b] = 0;
+          const unsigned long long old = atomicAdd(
+              reinterpret_cast<unsigned long long *>(g.ctl + kCtlTileClaim + (P & 1u)), 1ull);
+          next = (uint32_t)(old >> 32) == (uint32_t)P ? kBufs * ncta + (int)(uint32_t)old
+                                                      : cta + (t + kBufs) * ncta;
+          if (next >= ntiles || *(volatile int *)&sm.err != 0) next = -1;
+        }
+        next = __shfl_sync(0xFFFFFFFFu, next, 0);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        arm(next, b);
+        if (next >= 0) stage_band(next, b, (1u << kBands) - 1u);
+      }
     }
-    // (3) evaluate this thread's word of tile k
-    const bool ok = mbar_wait(smem_u32(&sm.full[buf]), (fpar >> buf) & 1u);
-    fpar ^= 1u << buf;
-    if (ok) {
-      if (threadIdx.x == 0) sm.staged &= ~(1u << buf);
-      phase_word<kRowTile>(g, local_u(buf), sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P,
-                           near128, keys);
-    } else {
-      sm.err = 1;
-    }
-    // this thread's shared-memory writes become visible to the bulk copies
-    // after the `done` handshake
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncwarp();
-    if (lane0) mbar_arrive(smem_u32(&sm.done[buf]));
-    buf = buf == kTileBufs - 1 ? 0 : buf + 1;
+    if constexpr (kSingle) break;  // one tile per CTA
+    b = b == kBufs - 1 ? 0 : b + 1;
     // leave together: the warp's lanes meet in __syncwarp every tile
     if (__any_sync(0xFFFFFFFFu, *(volatile int *)&sm.err != 0)) break;
   }
-  if (threadIdx.x == 0) {
-    if (!sm.err && k >= 1) {
-      // the last tile
-      const int pb = buf == 0 ? kTileBufs - 1 : buf - 1;
-      if (mbar_wait(smem_u32(&sm.done[pb]), (sm.dpar >> pb) & 1u))
-        write_back(tile - ncta, pb);
-      else
-        sm.err = 1;
-    }
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    if (sm.err) {
-      // give loads still in flight a bounded chance to land before exiting
-      mbar_wait(smem_u32(&sm.tables), 0u);
-      for (int b = 0; b < kTileBufs; ++b)
-        if (sm.staged & (1u << b)) mbar_wait(smem_u32(&sm.full[b]), (fpar >> b) & 1u);
-      g.ctl[kCtlStatus] = 1;
-    }
+  __syncthreads();
+  if (threadIdx.x == 0 && sm.err) {
+    // give loads still in flight a bounded chance to land before exiting: the
+    // last staging of every buffer (phases complete in order)
+    mbar_wait(smem_u32(&sm.tables), 0u);
+    for (int q = 0; q < kBufs; ++q)
+      if (sm.armed[q] > 0) mbar_wait(smem_u32(&sm.full[q]), (uint32_t)(sm.armed[q] - 1) & 1u);
+    g.ctl[kCtlStatus] = 1;
   }
 }
 
