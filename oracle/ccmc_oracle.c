@@ -273,21 +273,23 @@ void oracle_pair_delta(const uint8_t *st, int Lx, int Ly, int a, int b, int na, 
 
 /* One coupled-pair move (Sec. 3.1): q = S_a + S_b; |q| = 2 cannot change;
  * otherwise draw one configuration of the pair's q-set uniformly (the current
- * one included), then apply the Metropolis test to dE.  The pair's 32-bit
- * random word R holds a 16-bit choice v (bits 0-15) and the top half u_hi of
- * its 32-bit acceptance word (bits 16-31).
- *   choice: v mod |set| when v < 65532 (a multiple of 4 and of 6), else SLOW
- *           word 1 mod |set| when it is below 4294967292 (also a multiple of
- *           12), else the current configuration.
- *   test:   accept iff thr == 0xFFFFFFFF or (u_hi << 16 | u_lo) < thr, with
- *           u_lo the low 16 bits of SLOW word 0. */
-int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t R,
+ * one included), then apply the Metropolis test to dE.  The pair's random
+ * field v has 16 bits (the low half of F); s0, s1 are words 0 and 1 of its
+ * SLOW Philox block.
+ *   v < 65532 = 12 x 5461: the choice is v mod |set| (|set| = 4 or 6 divides
+ *           12) and w = floor(v / 12), uniform on [0, 5461) and independent of
+ *           v mod 12, is the acceptance word's top part: accept iff thr ==
+ *           0xFFFFFFFF or w 2^32 + s0 < 5461 thr (64-bit integers), which
+ *           happens with probability thr / 2^32.
+ *   v >= 65532: the choice is s1 mod |set| when s1 < 4294967292 (a multiple
+ *           of 12), else the current configuration; accept iff thr ==
+ *           0xFFFFFFFF or s0 < thr. */
+int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t F,
                      const uint32_t key[2], const uint32_t slow_ctr[4], const uint32_t *table) {
   int ca = st[a], cb = st[b];
   int q = CODE_S[ca] + CODE_S[cb];
   if (q == 2 || q == -2) return 0;
-  uint32_t v = R & 0xFFFFu;
-  uint32_t u_hi = R >> 16;
+  uint32_t v = F & 0xFFFFu;
   uint32_t slow[4];
   int have_slow = 0;
   const uint8_t(*set)[2] = (q == 1) ? SET_QP1 : (q == -1) ? SET_QM1 : SET_Q0;
@@ -320,8 +322,12 @@ int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t R,
       oracle_philox4x32_10(slow_ctr, key, slow);
       have_slow = 1;
     }
-    uint32_t u = (u_hi << 16) | (slow[0] & 0xFFFFu);
-    accept = u < thr;
+    if (v < 65532u) {
+      uint64_t w = v / 12u;
+      accept = (w << 32) + (uint64_t)slow[0] < (uint64_t)5461u * (uint64_t)thr;
+    } else {
+      accept = slow[0] < thr;
+    }
   }
   if (!accept) return 0;
   st[a] = (uint8_t)na;
@@ -366,10 +372,12 @@ static void write_record(const uint8_t *st, int Lx, int Ly, int64_t sweeps_done,
 
 /* ------------------------------------------------------------------------ */
 /* One colour phase: every pair (a, a + r), a = (4i + a0x, 4j + a0y), with pair
- * index k = j * (Lx/4) + i inside the class.  Pairs come in groups of four
- * consecutive i of one class row: pair (i, j) takes word i mod 4 of
- * Philox(seed, (j * ceil(Lx/16) + i/4, P_lo, P_hi, MOVE)), and its slow words
- * from Philox(seed, (k, P_lo, P_hi, SLOW)). */
+ * index k = j * (Lx/4) + i inside the class.  A class row is cut into blocks
+ * of 16 consecutive i, each served by two MOVE calls: pair (i, j) takes half
+ * (i mod 2) of word (i / 4) mod 4 of Philox(seed, (j * 2 ceil(Lx/64) +
+ * 2 floor(i/16) + (i / 2) mod 2, P_lo, P_hi, MOVE)) as its 16-bit field, so
+ * that one call serves the eight pairs with i mod 4 in {0, 1} (or {2, 3}) of a
+ * block; its slow words come from Philox(seed, (k, P_lo, P_hi, SLOW)). */
 void oracle_phase(uint8_t *st, int Lx, int Ly, uint64_t seed, uint64_t P, const uint32_t *table) {
   uint32_t key[2];
   seed_key(seed, key);
@@ -382,11 +390,11 @@ void oracle_phase(uint8_t *st, int Lx, int Ly, uint64_t seed, uint64_t P, const 
       int64_t k = (int64_t)j * Cx + i;
       int ax = 4 * i + a0x, ay = 4 * j + a0y;
       int bx = (ax + rx) % Lx, by = (ay + ry) % Ly;
-      int64_t group = (int64_t)j * ((Cx + 3) / 4) + i / 4;
-      uint32_t mctr[4] = {(uint32_t)group, Plo, Phi, ORACLE_TAG_MOVE};
+      int64_t call = (int64_t)j * 2 * ((Cx + 15) / 16) + 2 * (i / 16) + ((i / 2) % 2);
+      uint32_t mctr[4] = {(uint32_t)call, Plo, Phi, ORACLE_TAG_MOVE};
       uint32_t mw[4];
       oracle_philox4x32_10(mctr, key, mw);
-      uint32_t R = mw[i & 3];
+      uint32_t R = (mw[(i / 4) % 4] >> (16 * (i % 2))) & 0xFFFFu;
       uint32_t sctr[4] = {(uint32_t)k, Plo, Phi, ORACLE_TAG_SLOW};
       oracle_pair_move(st, Lx, Ly, ay * Lx + ax, by * Lx + bx, R, key, sctr, table);
     }
@@ -415,8 +423,8 @@ int64_t oracle_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0
 /* ------------------------------------------------------------------------ */
 /* Sequential random-pair mode (Sec. 3.1 as a serial algorithm): move t draws an
  * ordered pair index uniform on [0, N(N-1)) from Philox(seed, (t_lo, t_hi,
- * attempt, SEQ)) words 0-1 by multiply-high with rejection; word 2 is the
- * pair's random word. */
+ * attempt, SEQ)) words 0-1 by multiply-high with rejection; the low half of
+ * word 2 is the pair's random field. */
 int64_t oracle_sequential_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
                                  int64_t nsweeps, double beta, double Delta, double V, double J,
                                  int obs_every, int64_t *records) {
@@ -465,7 +473,8 @@ int64_t oracle_sequential_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int
  * (right, left, down, up), then makes the coupled-pair move of Sec. 3.1; N/2
  * moves per sweep.  Random words: Philox(seed, (t_lo, t_hi, attempt, NN)) with
  * t the global move index; words 0-1 give (a, direction) by Lemire's
- * multiply-high over 4N with rejection, word 2 is the pair's move word. */
+ * multiply-high over 4N with rejection, the low half of word 2 is the pair's
+ * random field. */
 int64_t oracle_neighbour_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int64_t sweep0,
                                 int64_t nsweeps, double beta, double Delta, double V, double J,
                                 int obs_every, int64_t *records) {
@@ -525,8 +534,8 @@ int64_t oracle_neighbour_sweeps(uint8_t *st, int Lx, int Ly, uint64_t seed, int6
  * Draws of map m: draw d uses words 2(d mod 2), 2(d mod 2) + 1 of
  * Philox(seed, (d / 2, m_lo, m_hi, MAP)) as a 64-bit x; the site is the high
  * word of x * N unless the low word is below 2^64 mod N (rejected: next d).
- * Moves: pair p of map m takes word 0 of Philox(seed, (p, m_lo, m_hi,
- * MAPMOVE)) as its move word and (p, m_lo, m_hi, MAPSLOW) as its slow
+ * Moves: pair p of map m takes the low half of word 0 of Philox(seed, (p,
+ * m_lo, m_hi, MAPMOVE)) as its random field and (p, m_lo, m_hi, MAPSLOW) as its slow
  * counter (oracle_pair_move). */
 int64_t oracle_map_size(int Lx, int Ly) {
   int64_t P = (int64_t)Lx * Ly / 10;

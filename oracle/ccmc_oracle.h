@@ -30,16 +30,16 @@ extern "C" {
 
 /* Counter-space tags (fourth counter word) of the independent random streams. */
 #define ORACLE_TAG_SCHED 1u   /* phase schedule (class a0 and offset r)     */
-#define ORACLE_TAG_MOVE 2u    /* per 4 pairs: one word each, choice | u_hi  */
-#define ORACLE_TAG_SLOW 3u    /* per pair: u_lo and the choice fallback     */
+#define ORACLE_TAG_MOVE 2u    /* per 8 pairs: a 16-bit field each          */
+#define ORACLE_TAG_SLOW 3u    /* per pair: acceptance word, choice fallback */
 #define ORACLE_TAG_FEISTEL 4u /* initial-state placement permutation        */
 #define ORACLE_TAG_SIGN 5u    /* initial spin signs of magnetic sites       */
-#define ORACLE_TAG_SEQ 6u     /* sequential random-pair mode: pair + u_hi   */
+#define ORACLE_TAG_SEQ 6u     /* sequential random-pair mode: pair + field  */
 #define ORACLE_TAG_SEQSLOW 7u /* sequential random-pair mode: slow words    */
-#define ORACLE_TAG_NN 8u      /* short-range pair mode: pair + u_hi        */
+#define ORACLE_TAG_NN 8u      /* short-range pair mode: pair + field       */
 #define ORACLE_TAG_NNSLOW 9u  /* short-range pair mode: slow words         */
 #define ORACLE_TAG_MAP 10u    /* paper maps: random-marking site draws      */
-#define ORACLE_TAG_MAPMOVE 11u /* paper maps: per pair, choice | u_hi       */
+#define ORACLE_TAG_MAPMOVE 11u /* paper maps: per pair, the 16-bit field    */
 #define ORACLE_TAG_MAPSLOW 12u /* paper maps: per pair, slow words          */
 #define ORACLE_TAG_PENALTY 13u /* penalty-function baseline: single sites   */
 
@@ -85,11 +85,11 @@ void oracle_schedule(int Lx, int Ly, uint64_t seed, uint64_t P, int *a0x, int *a
 void oracle_pair_delta(const uint8_t *st, int Lx, int Ly, int a, int b, int na, int nb,
                        int out[3]);
 
-/* One coupled-pair Metropolis move on sites a and b.  R is the pair's 32-bit
- * random word (16-bit choice, then the top half of the acceptance word); the
- * SLOW words are drawn from Philox(key, slow_ctr) when needed.  Returns 1 if
- * the lattice changed. */
-int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t R,
+/* One coupled-pair Metropolis move on sites a and b.  The low 16 bits of F
+ * are the pair's random field (choice and the acceptance word's top part,
+ * see ccmc_oracle.c); the SLOW words are drawn from Philox(key, slow_ctr)
+ * when needed.  Returns 1 if the lattice changed. */
+int oracle_pair_move(uint8_t *st, int Lx, int Ly, int a, int b, uint32_t F,
                      const uint32_t key[2], const uint32_t slow_ctr[4], const uint32_t *table);
 
 /* Full recount: out = {Nc, BV, BJ, M, M_stag, S_sum, S_stag}. */

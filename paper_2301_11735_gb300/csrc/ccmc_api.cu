@@ -102,17 +102,13 @@ int upload_params_on(ccmc_lattice *h, double beta, double Delta, double V, doubl
       h->params[3] == J)
     return CCMC_OK;
   std::vector<uint32_t> thr32(kTableN);
-  std::vector<uint32_t> thrhi(kThrHiWords, 0);
-  std::vector<uint16_t> thrhi16(kThrHi16, 0);
+  std::vector<uint16_t> thrT(kThrT, 0);
   build_thresholds(beta, Delta, V, J, thr32.data());
-  for (int i = 0; i < kTableN; ++i) thrhi[i] = thr32[i] & 0xFFFF0000u;
-  for (int i = 0; i < kTableN; ++i) thrhi16[i] = (uint16_t)(thr32[i] >> 16);
+  for (int i = 0; i < kTableN; ++i) thrT[i] = threshold_level(thr32[i]);
   CK(cudaMemcpyAsync(h->t.thr32, thr32.data(), sizeof(uint32_t) * kTableN,
                      cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(h->t.thrhi16, thrhi16.data(), sizeof(uint16_t) * kThrHi16,
-                     cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(h->t.thrhi, thrhi.data(), sizeof(uint32_t) * kThrHiWords,
-                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->t.thrT, thrT.data(), sizeof(uint16_t) * kThrT, cudaMemcpyHostToDevice,
+                     st));
   // pageable sources: the copies are staged before the calls return
   h->have_params = true;
   h->params[0] = beta;
@@ -266,7 +262,6 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   g.Cx = Lx / 4;
   g.Cy = Ly / 4;
   g.W = (g.Cx + 15) / 16;
-  g.Cx4 = (g.Cx + 3) / 4;
   g.cstride = (int64_t)g.Cy * g.W;
   const uint64_t N = (uint64_t)Lx * (uint64_t)Ly;
   g.rej = (0 - N) % N;
@@ -305,21 +300,15 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
       cudaMalloc(&h->d_ring, sizeof(int64_t) * 8 * h->ring_cap) != cudaSuccess ||
       cudaMalloc(&h->d_flag, sizeof(int)) != cudaSuccess)
     return fail(CCMC_E_NOMEM);
-  const size_t tb = sizeof(uint32_t) * (kTableN + 4 * kMoveN + kThrHiWords) +
-                    sizeof(uint16_t) * kThrHi16;
+  const size_t tb = sizeof(uint32_t) * (kTableN + 2 * kMoveN) + sizeof(uint16_t) * kThrT;
   if (cudaMalloc(&h->d_tables, tb) != cudaSuccess) return fail(CCMC_E_NOMEM);
-  // thrhi and the move table one after another (kStagedTableBytes, a
-  // multiple of 16 from a 256-byte aligned base): the tile kernel copies them
-  // into shared memory with one bulk copy; thr32 after them
+  // the threshold levels and the move table one after another (a multiple of
+  // 16 bytes from a 256-byte aligned base): the tile kernels copy them into
+  // shared memory with one bulk copy; thr32 after them
   char *p = (char *)h->d_tables;
-  h->t.thrhi = (uint32_t *)p;
-  p += sizeof(uint32_t) * kThrHiWords;
+  h->t.thrT = (uint16_t *)p;
+  p += sizeof(uint16_t) * kThrT;
   h->t.trans = (uint32_t *)p;
-  p += sizeof(uint32_t) * 2 * kMoveN;
-  // the compact tile kernel's copy: 16-bit tops, then the move table again
-  h->t.thrhi16 = (uint16_t *)p;
-  p += sizeof(uint16_t) * kThrHi16;
-  h->t.trans16 = (uint32_t *)p;
   p += sizeof(uint32_t) * 2 * kMoveN;
   h->t.thr32 = (uint32_t *)p;
   g.words = h->d_words;
@@ -327,8 +316,6 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
   uint32_t tr[2 * kMoveN];
   if (!build_transitions(tr)) return fail(CCMC_E_INVAL);
   if (cudaMemcpyAsync(h->t.trans, tr, sizeof(tr), cudaMemcpyHostToDevice, h->stream) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(h->t.trans16, tr, sizeof(tr), cudaMemcpyHostToDevice, h->stream) !=
           cudaSuccess ||
       cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t) * 16 * g.cstride, h->stream) !=
           cudaSuccess ||
@@ -642,7 +629,7 @@ namespace {
 JobDesc job_of(ccmc_lattice *h, int64_t nsweeps, int obs_every) {
   JobDesc d{};
   d.g = h->g;
-  d.thrhi = h->t.thrhi;
+  d.thrT = h->t.thrT;
   d.thr32 = h->t.thr32;
   d.trans = h->t.trans;
   d.nsweeps = nsweeps;
@@ -736,7 +723,7 @@ int run_multi(ccmc_batch *b, MultiGroup &G, int64_t nsweeps, int obs_every) {
     }
     MultiJob j{};
     j.g = h->g;
-    j.thrhi = h->t.thrhi;
+    j.thrT = h->t.thrT;
     j.thr32 = h->t.thr32;
     j.trans = h->t.trans;
     j.cta_begin = begin;

@@ -13,8 +13,8 @@ struct ccmc_batch;
 namespace ccmc {
 
 constexpr uint32_t TAG_SCHED = 1u;    // phase schedule
-constexpr uint32_t TAG_MOVE = 2u;     // per 4-pair group: one word a pair
-constexpr uint32_t TAG_SLOW = 3u;     // per pair: u_lo, choice fallback
+constexpr uint32_t TAG_MOVE = 2u;     // per 8 pairs: a 16-bit field a pair
+constexpr uint32_t TAG_SLOW = 3u;     // per pair: acceptance word, choice fallback
 constexpr uint32_t TAG_FEISTEL = 4u;  // initial placement
 constexpr uint32_t TAG_SIGN = 5u;     // initial spin signs
 
@@ -39,7 +39,6 @@ struct Geo {
   uint32_t *words;  // 16 classes x Cy rows x W words
   int64_t *ctl;     // control block
   int Lx, Ly, Cx, Cy, W;
-  int Cx4;          // ceil(Cx / 4): 4-pair random groups per class row
   int64_t cstride;  // Cy * W words per class
   uint32_t k0, k1;  // Philox key = seed
   uint64_t rej;     // 2^64 mod (Lx Ly): Lemire rejection bound
@@ -47,12 +46,17 @@ struct Geo {
 
 // Per-lattice parameter tables in device memory (built on the host).
 struct DevTables {
-  uint32_t *thrhi;      // kThrHiWords: each threshold with its low half cleared (fast path)
-  uint32_t *thr32;      // kTableN: full thresholds (exact path)
-  uint32_t *trans;      // kMoveN x 2 words: move entries (see kMoveN)
-  uint16_t *thrhi16;    // kThrHi16: each threshold's top 16 bits (compact fast path)
-  uint32_t *trans16;    // a copy of trans directly after thrhi16 (staged with it)
+  uint16_t *thrT;   // kThrT: threshold levels T = floor(5461 thr / 2^32), 5461 for
+                    // thr = 0xFFFFFFFF (fast path)
+  uint32_t *trans;  // kMoveN x 2 words: move entries (see kMoveN), directly after thrT
+  uint32_t *thr32;  // kTableN: full thresholds (exact path)
 };
+
+// The fast path's threshold level of a 32-bit threshold: a field's w = v / 12
+// (in [0, 5461)) below it accepts, above it rejects, equal to it is a tie.
+__host__ __device__ inline uint16_t threshold_level(uint32_t thr) {
+  return thr == 0xFFFFFFFFu ? (uint16_t)5461 : (uint16_t)(((uint64_t)thr * 5461u) >> 32);
+}
 
 // Move entries: one uint2 per (r, near, pc), entry (2 r + near) * 16 + pc, i.e.
 // at byte offset 256 r + 128 near + 8 pc -- r the pair's choice field mod 12
@@ -60,8 +64,7 @@ struct DevTables {
 // nearest neighbour, pc = 4 code_a + code_b the pair state.
 constexpr int kTransN = 16 * 12;     // entries of one kind (far or near)
 constexpr int kMoveN = 2 * kTransN;  // both kinds
-constexpr int kThrHiWords = (kTableN + 1) / 2 * 2;  // padded to an even count
-constexpr int kThrHi16 = (kTableN + 7) / 8 * 8;     // 16-bit tops, padded to 16 bytes
+constexpr int kThrT = (kTableN + 7) / 8 * 8;  // 16-bit levels, padded to 16 bytes
 
 struct LaunchCfg {
   int phase_grid_cap = 152 * 3;  // one resident wave of phase_kernel (set at create)
@@ -72,7 +75,7 @@ struct LaunchCfg {
 // One lattice of a resident batch launch (device array, filled on the host).
 struct JobDesc {
   Geo g;                    // the lattice in global memory
-  const uint32_t *thrhi;    // its tables
+  const uint16_t *thrT;     // its tables
   const uint32_t *thr32;
   const uint32_t *trans;
   int64_t nsweeps;          // sweeps to run in this launch
@@ -81,20 +84,21 @@ struct JobDesc {
   int64_t *hist;            // histograms (nullptr: none)
   int nbins;
   int obs_every;
+  int tpw;                  // threads a word: 1, 2 or 4 (0: by the lattice's size)
 };
 
 // One lattice of a lock-step multi-lattice phase launch: CTAs
 // [cta_begin, cta_begin + cta_count) of the grid work on it.
 struct MultiJob {
   Geo g;
-  const uint32_t *thrhi;
+  const uint16_t *thrT;
   const uint32_t *thr32;
   const uint32_t *trans;
   int cta_begin, cta_count;
 };
 
 // Shared memory of the resident kernel besides the lattice words.
-constexpr int kResTableWords = kThrHiWords + 2 * kMoveN;
+constexpr int kResTableWords = kThrT / 2 + 2 * kMoveN;
 
 // Host-side table builders (ccmc_tables.cpp).
 void build_thresholds(double beta, double Delta, double V, double J, uint32_t *thr32);

@@ -8,10 +8,10 @@
 // The move uses the library's own tables: the 64-bit move entry of the pair's
 // state, choice and kind (partner a nearest neighbour of a or not), the dp4a threshold index from (sum_a (S+1) - sum_b (S+1) + 8,
 // sum_a (sigma+1), sum_b (sigma+1)) and the full 32-bit threshold.  Random
-// words of pair p of map m: R = word 0 of Philox(seed, (p, m_lo, m_hi, 11))
-// (bits 0-15 the choice v, bits 16-31 the acceptance word's top half) and,
-// when v >= 65532 or the top halves tie, the slow words of Philox(seed, (p,
-// m_lo, m_hi, 12)) -- the same rules as the colour phases' exact path.
+// words of pair p of map m: the 16-bit field v = the low half of word 0 of
+// Philox(seed, (p, m_lo, m_hi, 11)) and, when v >= 65532 or its level w =
+// v / 12 ties the threshold's level, the slow words of Philox(seed, (p, m_lo,
+// m_hi, 12)) -- the same rules as the colour phases' exact path.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) map_kernel(Geo g, const int32_t *__restri
     }
   }
   const U4 rw = philox((uint32_t)p, m_lo, m_hi, kTagMapMove, g.k0, g.k1);
-  const uint32_t R = rw.x, v = R & 0xFFFFu;
+  const uint32_t v = rw.x & 0xFFFFu, wq = v / 12u;
   U4 sl{0u, 0u, 0u, 0u};
   bool have_slow = false;
   uint32_t r;
@@ -96,18 +96,20 @@ __global__ void __launch_bounds__(256) map_kernel(Geo g, const int32_t *__restri
   }
   const uint32_t pc = (ca << 2) | cb;
   const uint2 e = trans[(2u * r + (near ? 1u : 0u)) * 16u + pc];
-  const uint32_t x = e.y >> 28;  // pc XOR the chosen configuration
+  const uint32_t x = (e.y >> 24) & 15u;  // pc XOR the chosen configuration
   if (x == 0u) return;           // the chosen configuration is the current one
   const uint32_t env = (SA + 8u - SB) | (GA << 8) | (GB << 16);
   const uint32_t thr = thr32[__dp4a((int)e.y, (int)env, (int)e.x)];
   bool accept;
   if (thr == 0xFFFFFFFFu) {
     accept = true;
-  } else if ((R >> 16) != (thr >> 16)) {
-    accept = (R >> 16) < (thr >> 16);
+  } else if (v >= 65532u) {
+    accept = sl.x < thr;  // have_slow: drawn for the choice
+  } else if (wq != threshold_level(thr)) {
+    accept = wq < threshold_level(thr);
   } else {
     if (!have_slow) sl = philox((uint32_t)p, m_lo, m_hi, kTagMapSlow, g.k0, g.k1);
-    accept = ((R & 0xFFFF0000u) | (sl.x & 0xFFFFu)) < thr;
+    accept = ((uint64_t)wq << 32) + sl.x < 5461ull * thr;
   }
   if (!accept) return;
   if (x >> 2) atomicXor(ra.word, (x >> 2) << ra.shift);

@@ -15,23 +15,30 @@
 namespace ccmc {
 
 // ============================================================================
-// One colour phase (Sec. 3.1-3.2).  Each thread owns one word of the a-class:
-// up to 16 pairs (a, a + r).  It reads the a word, the four neighbour windows
-// of a, the b window and the four neighbour windows of b; evaluates every
-// pair's move; stores the a word and XORs the changed b sites back.
+// One colour phase (Sec. 3.1-3.2).  A word of the a-class holds 16 pairs
+// (a, a + r), site t of the word at bits 2t..2t+1.  Its pairs are read as the
+// a word, the four neighbour windows of a, the b window and the four neighbour
+// windows of b; every pair's move is evaluated; the a word is stored and the
+// changed b sites are XORed back.
 //
-// Per pair, with pc = 4 code_a + code_b and its 32-bit random word R (16-bit
-// choice v in the low half, top half u of the acceptance word in the high):
-//   entry  = trans[v mod 12][near][pc]  -> base, byte coefficients, pc XOR npc
+// Random fields: pair t takes the 16-bit half (t mod 2) of word (t / 4) mod 4
+// of MOVE call c = (t / 2) mod 2 of its word, i.e. call c serves the pair
+// groups k = 2c (low halves) and k = 2c + 1 (high halves), group k being the
+// sites k, k + 4, k + 8, k + 12 (lane q = site / 4).  Per pair, with pc =
+// 4 code_a + code_b and its field v:
+//   w      = floor(v / 12), the choice class v - 12 w (v < 65532 = 12 x 5461)
+//   entry  = trans[v - 12 w][near][pc] -> base, byte coefficients, pc XOR npc
 //   index  = dp4a(coefficients, (D8, GA, GB, 0), base)  (threshold index)
-//   accept = R < thrhi[index], i.e. u < the threshold's top half (v < 2^16)
-// The fast decision is always applied.  A tie of the top halves, or a choice
-// field v >= 65532, makes the word rare: the exact path then re-examines its
-// pairs and, for each truly rare one, undoes the fast decision and applies the
-// exact one with the pair's SLOW random words (about one pair in 10^4).
+//   accept = w < T[index], with T = floor(5461 thr / 2^32) (5461 when thr is
+//            0xFFFFFFFF): w < T implies w 2^32 + s < 5461 thr for every 32-bit
+//            s, w > T the opposite
+// The fast decision is always applied.  A tie (w == T) or a field v >= 65532
+// sends the call's pairs through the exact path, which decides each truly rare
+// pair (the fast path rejected it) with its SLOW random words (about one pair
+// in 4000).
 struct PhaseSmem {
   uint2 trans[kMoveN];
-  uint32_t thrhi[kThrHiWords];
+  uint16_t thrT[kThrT];
   Sched sched;
 };
 
@@ -44,9 +51,9 @@ struct PhaseU {
   int wmask;  // W - 1 (rows of power-of-two width only)
 };
 
-// How phase_word reads its windows: rows of any width (kRowGeneral), rows of
-// whole words (kRowAligned), or rows of whole words and power-of-two width W,
-// staged as bands whose first row is the tile's first row (kRowTile: column
+// How the word code reads its windows: rows of any width (kRowGeneral), rows
+// of whole words (kRowAligned), or rows of whole words and power-of-two width
+// W, staged as bands whose first row is the tile's first row (kRowTile: column
 // wraps are masks and every row offset dy is 0).
 enum RowMode { kRowGeneral = 0, kRowAligned = 1, kRowTile = 2 };
 
@@ -103,94 +110,150 @@ __device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, co
 }
 
 // Move entry of choice class r (v mod 12) and pc8 = 8 pc + 128 near: byte
-// offset 256 r + pc8 of the move table.
+// offset 256 r + pc8 of the move table.  Word 0: the threshold index's base;
+// word 1: the signed byte coefficients of (D8, GA, GB) and, at bits 24-27 (the
+// byte dp4a multiplies by zero), the move pc XOR npc.
 __device__ __forceinline__ uint2 move_entry(const uint2 *trans, uint32_t r, uint32_t pc8) {
   return *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(trans) + r * 256u + pc8);
 }
 
-// v mod 12 for v < 2^16: v - 12 floor(v / 12), the quotient by a multiply-high
-// (floor(v m / 2^32) with m = ceil(2^32 / 12) is exact for v < 2^16).
-__device__ __forceinline__ uint32_t mod12(uint32_t v) {
-  return v - 12u * __umulhi(v, 357913942u);
-}
+// floor(v / 12) for v < 2^16 by a multiply-high: floor(v m / 2^32) with
+// m = ceil(2^32 / 12) is exact there.
+__device__ __forceinline__ uint32_t div12(uint32_t v) { return __umulhi(v, 357913942u); }
 
-// The top half of the threshold at idx, in the high 16 bits (the low 16 are
-// zero): from a table of 32-bit words with the low halves cleared, or of
-// 16-bit tops (half the shared memory, one shift more).
-__device__ __forceinline__ uint32_t thr_top(const uint32_t *thrhi, int idx) { return thrhi[idx]; }
-__device__ __forceinline__ uint32_t thr_top(const uint16_t *thrhi, int idx) {
-  return (uint32_t)thrhi[idx] << 16;
-}
+// The pair's move nibble (a bits 2-3, b bits 0-1) in an entry's word 1.
+__device__ __forceinline__ uint32_t move_nibble(uint32_t ey) { return (ey >> 24) & 15u; }
 
-// Byte lanes of a word's groups (see phase_word): x01/x23 hold (D8, GA) of
-// pairs 0, 1 / 2, 3 of group k, gb the GB of its four pairs.
-struct GroupEnv {
-  uint32_t x01[4], x23[4], gb[4];
+// Byte lanes of one pair group (sites k, k + 4, k + 8, k + 12): x01/x23 hold
+// (D8, GA) of lanes 0, 1 / 2, 3, gb the GB of its four lanes, pc8 the
+// move-table offsets 8 pc + near128.
+struct Group {
+  uint32_t x01, x23, gb, pc8;
 };
 
-// dp4a operand (D8, GA, GB, 0) of pair t = 4 b + k (t, b, k compile-time
-// constants in the main loop).
-__device__ __forceinline__ uint32_t pair_env(const GroupEnv &ge, int b, int k) {
-  return b == 0 ? prmt(ge.x01[k], ge.gb[k], 0x8410u)
-       : b == 1 ? prmt(ge.x01[k], ge.gb[k], 0x8532u)
-       : b == 2 ? prmt(ge.x23[k], ge.gb[k], 0x8610u)
-                : prmt(ge.x23[k], ge.gb[k], 0x8732u);
+__device__ __forceinline__ Group group_env(const Sums &sa, const Sums &sb, uint32_t pcE,
+                                           uint32_t pcO, uint32_t near128, int k) {
+  const uint32_t d8 = group_bytes(sa.se, sa.so, k) + 0x08080808u - group_bytes(sb.se, sb.so, k);
+  const uint32_t ga = group_bytes(sa.ge, sa.go, k);
+  Group gr;
+  gr.gb = group_bytes(sb.ge, sb.go, k);
+  gr.x01 = prmt(d8, ga, 0x5140u);
+  gr.x23 = prmt(d8, ga, 0x7362u);
+  gr.pc8 = group_bytes(pcE, pcO, k) * 8u + near128 * 0x01010101u;
+  return gr;
 }
 
-// The exact path of a word (see phase_word): for each pair of the flagged
-// groups (bit t of slow) whose fast decision is not certain, undo it and apply
-// the exact one; returns the corrected (dA, dB).
-template <bool kAligned, class ThrT>
-__device__ __forceinline__ uint2 exact_path(const uint2 *trans, const ThrT *thrhi,
-                                            const uint32_t *thr32, uint32_t k0, uint32_t k1,
-                                            uint32_t gbase, uint32_t slow0, int n, uint64_t P,
-                                            uint32_t near128, uint32_t A, uint32_t B, Sums sa,
-                                            Sums sb, uint32_t slow, uint32_t dA, uint32_t dB) {
-  U4 mv{0u, 0u, 0u, 0u};
-  int mv_group = -1;
-  while (slow) {
-    const int t = __ffs(slow) - 1;
-    slow &= slow - 1u;
-    if (!kAligned && t >= n) continue;
-    if ((t >> 2) != mv_group) {
-      mv_group = t >> 2;
-      mv = philox(gbase + (uint32_t)mv_group, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, k0, k1);
+// dp4a operand (D8, GA, GB, 0) of lane q of a group (q a compile-time constant
+// in the unrolled loops).
+__device__ __forceinline__ uint32_t lane_env(const Group &gr, int q) {
+  return q == 0 ? prmt(gr.x01, gr.gb, 0x8410u)
+       : q == 1 ? prmt(gr.x01, gr.gb, 0x8532u)
+       : q == 2 ? prmt(gr.x23, gr.gb, 0x8610u)
+                : prmt(gr.x23, gr.gb, 0x8732u);
+}
+
+// The pairs of a word one thread evaluates: kTPW threads share a word (1, 2 or
+// 4), thread `sub` of them takes MOVE call(s) and half(s):
+//   kTPW 1: both calls, both halves (all 16 pairs);
+//   kTPW 2: call sub, both halves (8 pairs);
+//   kTPW 4: call sub / 2, half sub mod 2 (4 pairs: group k = sub).
+// Returns the word's (dA, dB) contribution of those pairs.
+template <int kMode, int kTPW, class Keys>
+__device__ __forceinline__ uint2 word_moves(const Geo &g, const uint2 *trans,
+                                            const uint16_t *thrT, const uint32_t *thr32, int j,
+                                            int w, int sub, uint32_t A, uint32_t B,
+                                            const Sums &sa, const Sums &sb, uint64_t P,
+                                            uint32_t near128, const Keys &keys) {
+  static_assert(kTPW == 1 || kTPW == 2 || kTPW == 4, "one, two or four threads a word");
+  constexpr int kCalls = kTPW == 1 ? 2 : 1;
+  constexpr int kHalves = kTPW == 4 ? 1 : 2;
+  const int c0 = kTPW == 1 ? 0 : (kTPW == 2 ? sub : sub >> 1);
+  const int h0 = kTPW == 4 ? (sub & 1) : 0;
+  const uint32_t pcE = ((A & 0x33333333u) << 2) | (B & 0x33333333u);
+  const uint32_t pcO = (A & 0xCCCCCCCCu) | ((B >> 2) & 0x33333333u);
+  const uint32_t gbase = (uint32_t)j * (uint32_t)(2 * g.W) + (uint32_t)(2 * w);
+  uint32_t dA = 0u, dB = 0u, slow = 0u;  // slow, bit c: call c needs the exact path
+#pragma unroll
+  for (int ci = 0; ci < kCalls; ++ci) {
+    const int c = c0 + ci;
+    const U4 r = keys(gbase + (uint32_t)c, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE);
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;  // smallest w - T, largest v of the call
+#pragma unroll
+    for (int hi = 0; hi < kHalves; ++hi) {
+      const int h = h0 + hi;
+      const int k = 2 * c + h;
+      const Group gr = group_env(sa, sb, pcE, pcO, near128, k);
+      uint32_t acc = 0u;  // byte q: the accepted move of lane q
+      uint32_t d0 = 0xFFFFFFFFu, v0 = 0u;
+#pragma unroll
+      for (int q = 3; q >= 0; --q) {
+        const uint32_t X = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
+        const uint32_t v = h ? X >> 16 : X & 0xFFFFu;
+        const uint32_t wq = div12(v);
+        const uint2 e = move_entry(trans, v - 12u * wq, prmt(gr.pc8, 0u, 0x4440u + (uint32_t)q));
+        const uint32_t T = thrT[__dp4a((int)e.y, (int)lane_env(gr, q), (int)e.x)];
+        const uint32_t d = wq - T;  // negative: accept; zero: a tie
+        if (q & 1) {
+          d0 = d;
+          v0 = v;
+        } else {
+          mn = __vimin3_u32(mn, d0, d);
+          mx = __vimax3_u32(mx, v0, v);
+        }
+        acc = __funnelshift_l((int)d < 0 ? e.y : 0u, acc, 8);
+      }
+      // byte q of acc -> site k + 4 q: b bits to 2 (k + 4 q) of dB, a bits of dA
+      const uint32_t bpart = acc & 0x03030303u, apart = (acc >> 2) & 0x03030303u;
+      dB |= bpart << (2 * k);
+      dA |= apart << (2 * k);
     }
-    const int qw = t & 3;
-    const uint32_t R = qw == 0 ? mv.x : qw == 1 ? mv.y : qw == 2 ? mv.z : mv.w;
-    const uint32_t pc = (((A >> (2 * t)) & 3u) << 2) | ((B >> (2 * t)) & 3u);
-    const uint32_t pc8 = pc * 8u + near128;
-    const uint32_t v = R & 0xFFFFu, uh = R >> 16;
-    const int sh = 4 * (t >> 1);
-    const uint32_t sa4 = (((t & 1) ? sa.so : sa.se) >> sh) & 15u;
-    const uint32_t sb4 = (((t & 1) ? sb.so : sb.se) >> sh) & 15u;
-    const uint32_t ga4 = (((t & 1) ? sa.go : sa.ge) >> sh) & 15u;
-    const uint32_t gb4 = (((t & 1) ? sb.go : sb.ge) >> sh) & 15u;
-    const uint32_t env = (sa4 + 8u - sb4) | (ga4 << 8) | (gb4 << 16);
-    // the fast path's decision for this pair
-    const uint2 ef = move_entry(trans, mod12(v), pc8);
-    const uint32_t THf = thr_top(thrhi, __dp4a((int)ef.y, (int)env, (int)ef.x));
-    if (R - THf >= 0x10000u && v < 65532u) continue;  // not rare: the fast decision stands
-    if (R < THf) {  // undo it
-      const uint32_t x = ef.y >> 28;
-      dA ^= (x >> 2) << (2 * t);
-      dB ^= (x & 3u) << (2 * t);
-    }
-    const U4 sl = philox(slow0 + (uint32_t)t, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, k0, k1);
-    uint32_t rc;
-    if (v < 65532u)
-      rc = mod12(v);
-    else if (sl.y < 4294967292u)
-      rc = sl.y % 12u;
-    else
-      continue;  // keep the current configuration
-    const uint2 e = move_entry(trans, rc, pc8);
-    const uint32_t thr = thr32[__dp4a((int)e.y, (int)env, (int)e.x)];
-    const uint32_t uu = (uh << 16) | (sl.x & 0xFFFFu);
-    if (thr == 0xFFFFFFFFu || uu < thr) {
-      const uint32_t x = e.y >> 28;
-      dA ^= (x >> 2) << (2 * t);
-      dB ^= (x & 3u) << (2 * t);
+    if (mn == 0u || mx >= 65532u) slow |= 1u << c;
+  }
+
+  // ---- exact path for the flagged calls (a tie or a field >= 65532)
+  if (slow) {
+    const uint32_t slow0 = (uint32_t)((uint64_t)j * g.Cx + (uint32_t)(w << 4));
+#pragma unroll 1
+    for (int ci = 0; ci < kCalls; ++ci) {
+      const int c = c0 + ci;
+      if (!((slow >> c) & 1u)) continue;
+      const U4 r = philox(gbase + (uint32_t)c, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0,
+                          g.k1);
+#pragma unroll 1
+      for (int hi = 0; hi < kHalves; ++hi) {
+        const int h = h0 + hi;
+        const int k = 2 * c + h;
+        const Group gr = group_env(sa, sb, pcE, pcO, near128, k);
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t X = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
+          const uint32_t v = h ? X >> 16 : X & 0xFFFFu;
+          const uint32_t wq = div12(v);
+          const uint32_t pc8 = prmt(gr.pc8, 0u, 0x4440u + (uint32_t)q);
+          const uint32_t env = prmt(q < 2 ? gr.x01 : gr.x23, gr.gb,
+                                    0x8410u + ((q & 1) ? 0x0122u : 0u) + ((q & 2) ? 0x0200u : 0u));
+          const uint2 ef = move_entry(trans, v - 12u * wq, pc8);
+          if (v < 65532u && wq != thrT[__dp4a((int)ef.y, (int)env, (int)ef.x)]) continue;
+          // a rare pair: the fast path rejected it; decide it exactly
+          const int t = k + 4 * q;
+          const U4 sl = philox(slow0 + (uint32_t)t, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW,
+                               g.k0, g.k1);
+          uint2 e = ef;
+          if (v >= 65532u) {
+            if (sl.y >= 4294967292u) continue;  // keep the current configuration
+            e = move_entry(trans, sl.y % 12u, pc8);
+          }
+          const uint32_t thr = thr32[__dp4a((int)e.y, (int)env, (int)e.x)];
+          const bool accept =
+              thr == 0xFFFFFFFFu ||
+              (v < 65532u ? ((uint64_t)wq << 32) + sl.x < 5461ull * thr : sl.x < thr);
+          if (accept) {
+            const uint32_t x = move_nibble(e.y);
+            dA ^= (x >> 2) << (2 * t);
+            dB ^= (x & 3u) << (2 * t);
+          }
+        }
+      }
     }
   }
   return make_uint2(dA, dB);
@@ -200,12 +263,13 @@ __device__ __forceinline__ uint2 exact_path(const uint2 *trans, const ThrT *thrh
 // a word in u's arrays (j itself for the lattice in global memory, the row
 // inside a staged tile otherwise); near128: 128 if the phase's partners are
 // nearest neighbours, else 0; keys: the source of the Philox keys (SeedKeys or
-// TableKeys of the lattice's seed).
-template <int kMode, class Keys = SeedKeys, class ThrT = uint32_t>
+// TableKeys of the lattice's seed); kTPW threads share the word, this one is
+// thread `sub` of them (see word_moves).
+template <int kMode, int kTPW = 1, class Keys = SeedKeys>
 __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
-                                           const ThrT *thrhi, const uint32_t *thr32, int j,
+                                           const uint16_t *thrT, const uint32_t *thr32, int j,
                                            int jr, int w, uint64_t P, uint32_t near128,
-                                           const Keys &keys) {
+                                           const Keys &keys, int sub = 0) {
   constexpr bool kAligned = kMode != kRowGeneral;
   // row jr + dy of a class (periodic in Cy); staged bands start at the right row
   auto row = [&](int r0, int dy) { return kMode == kRowTile ? r0 : wrap(r0 + dy, g.Cy); };
@@ -224,99 +288,25 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
                                  window<kMode>(u.cBR, g, u, jb, w, u.offBR, n),
                                  window<kMode>(u.cBU, g, u, row(jb, u.dyBU), w, u.offB, n),
                                  window<kMode>(u.cBD, g, u, row(jb, u.dyBD), w, u.offB, n));
-
-  // ---- pair states in 4-bit lanes: lane u of pcE is site 2u, of pcO site 2u+1
-  const uint32_t pcE = ((A & 0x33333333u) << 2) | (B & 0x33333333u);
-  const uint32_t pcO = (A & 0xCCCCCCCCu) | ((B >> 2) & 0x33333333u);
-
-  // ---- byte lanes of group k (sites k, k+4, k+8, k+12): D8 = SA - SB + 8, GA,
-  // GB, and the move-table offsets 8 pc + near128 of the group's pairs
-  GroupEnv ge;
-  uint32_t pck[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t d8 = group_bytes(sa.se, sa.so, k) + 0x08080808u - group_bytes(sb.se, sb.so, k);
-    const uint32_t ga = group_bytes(sa.ge, sa.go, k);
-    ge.gb[k] = group_bytes(sb.ge, sb.go, k);
-    ge.x01[k] = prmt(d8, ga, 0x5140u);
-    ge.x23[k] = prmt(d8, ga, 0x7362u);
-    pck[k] = group_bytes(pcE, pcO, k) * 8u + near128 * 0x01010101u;
-  }
-
-  // ---- random words: pair (i, j) of the class takes word i mod 4 of
-  // Philox(seed, (j Cx4 + i / 4, P_lo, P_hi, MOVE)); call b covers pairs 4b..4b+3.
-  // Accepted moves (pc XOR npc, bits 28-31 of the entry) are shifted into accE
-  // (even pairs) and accO (odd pairs): pair 2m ends in lane m of accE.
-  const uint32_t gbase = (uint32_t)j * (uint32_t)g.Cx4 + (uint32_t)(4 * w);
-  uint32_t accE = 0u, accO = 0u;
-  uint32_t slow = 0u;  // bit t: pair t's group needs the exact path
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    if (!kAligned && 4 * b >= n) break;
-    uint32_t mn = 0xFFFFFFFFu, mx = 0u;  // smallest R - TH, largest v of the group
-    const U4 r = keys(gbase + (uint32_t)b, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE);
-    uint32_t d0 = 0xFFFFFFFFu, v0 = 0u;  // pair k - 1's (k odd)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int t = 4 * b + k;
-      if (!kAligned && t >= n) {  // past the end of the row: no pair
-        if (k & 1) {
-          mn = min(mn, d0);
-          mx = max(mx, v0);
-        }
-        continue;
-      }
-      const uint32_t R = k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w;
-      const uint32_t env = pair_env(ge, b, k);
-      const uint32_t pc8 = prmt(pck[k], 0u, 0x4440u + (uint32_t)b);
-      const uint32_t v = R & 0xFFFFu;
-      const uint2 e = move_entry(trans, mod12(v), pc8);
-      const uint32_t TH = thr_top(thrhi, __dp4a((int)e.y, (int)env, (int)e.x));
-      const uint32_t d = R - TH;  // < 2^16 iff the top halves tie (TH's low half is 0)
-      if (k & 1) {
-        mn = __vimin3_u32(mn, d0, d);
-        mx = __vimax3_u32(mx, v0, v);
-      } else {
-        d0 = d;
-        v0 = v;
-      }
-      const uint32_t xm = R < TH ? (e.y & 0xF0000000u) : 0u;
-      if (t & 1)
-        accO = (accO >> 4) | xm;
-      else
-        accE = (accE >> 4) | xm;
-    }
-    // a tie of the top halves (R - TH < 2^16) or a choice field v >= 65532
-    // sends the group's pairs through the exact path
-    if (mn < 0x10000u || mx >= 65532u) slow |= 0xFu << (4 * b);
-  }
+  const uint2 d = word_moves<kMode, kTPW>(g, trans, thrT, thr32, j, w, sub, A, B, sa, sb, P,
+                                          near128, keys);
+  uint32_t dA = d.x, dB = d.y;
   if constexpr (!kAligned) {
-    // lanes of missing pairs were never shifted in: align pair 0 to lane 0
-    const int ne = (n + 1) >> 1, no = n >> 1;
-    if (ne < 8) accE = ne == 0 ? 0u : accE >> (4 * (8 - ne));
-    if (no < 8) accO = no == 0 ? 0u : accO >> (4 * (8 - no));
-  }
-  uint32_t dA = ((accE >> 2) & 0x33333333u) | (((accO >> 2) & 0x33333333u) << 2);
-  uint32_t dB = (accE & 0x33333333u) | ((accO & 0x33333333u) << 2);
-
-  // ---- exact path for the flagged groups (about one group in 10^4)
-  if (slow) {
-    const uint2 d = exact_path<kAligned>(trans, thrhi, thr32, g.k0, g.k1, gbase,
-                                         (uint32_t)((uint64_t)j * g.Cx + s0), n, P, near128, A,
-                                         B, sa, sb, slow, dA, dB);
-    dA = d.x;
-    dB = d.y;
-  }
-  if constexpr (!kAligned) {
-    if (n < 16) {
+    if (n < 16) {  // pairs past the end of the row do not exist
       const uint32_t valid = (1u << (2 * n)) - 1u;
       dA &= valid;
       dB &= valid;
     }
   }
 
-  // ---- write back: the a word is this thread's alone; the b sites share words
-  if (dA) rowA[w] = A ^ dA;
+  // ---- write back: the a word is this thread's alone unless threads share
+  // it; the b sites share words with neighbouring words' partners
+  if (dA) {
+    if constexpr (kTPW == 1)
+      rowA[w] = A ^ dA;
+    else
+      atomicXor(rowA + w, dA);
+  }
   if (dB) {
     uint32_t *rb = const_cast<uint32_t *>(u.cB) + jb * g.W;
     if constexpr (kMode == kRowTile) {
@@ -342,14 +332,15 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
 }
 
 template <bool kAligned>
-__global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *thrhi,
+__global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint16_t *thrT,
                                                     const uint32_t *thr32, const uint32_t *trans,
                                                     int64_t p_off) {
   __shared__ PhaseSmem sm;
   // The tables come from host uploads that precede the whole launch chain, so
   // they are loaded before waiting for the previous kernel of the stream (which
   // lets this prologue overlap its tail under programmatic dependent launch).
-  for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) sm.thrhi[t] = thrhi[t];
+  for (int t = threadIdx.x; t < kThrT / 2; t += blockDim.x)
+    reinterpret_cast<uint32_t *>(sm.thrT)[t] = reinterpret_cast<const uint32_t *>(thrT)[t];
   asm volatile("griddepcontrol.wait;" ::: "memory");
   // The next kernel may launch now: with one resident wave its blocks only take
   // the slots of blocks that finish, and it waits for this whole grid before
@@ -373,7 +364,7 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint32_t *th
   int j = wid / g.W, w = wid - j * g.W;
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
-    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, thr32, j, j, w, P,
+    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrT, thr32, j, j, w, P,
                                                       near128, SeedKeys{g.k0, g.k1});
     w += sw;
     j += sj;
@@ -424,16 +415,10 @@ constexpr uint32_t kWaitSpins = 1u << 24;              // bounded mbarrier waits
 constexpr unsigned long long kWaitNs = 1000000000ull;  // at most 2^24 polls or 1 s
 constexpr uint32_t kSuspendNs = 20000;                 // suspend-time hint of a poll
 
-// The lattice's threshold tops and the move table, contiguous in device
-// memory (thrhi, trans -- or the compact copy thrhi16, trans16), staged with
-// one bulk copy.  ThrT: uint32_t (tops in 32-bit words) or uint16_t (16-bit
-// tops: 10 KB less shared memory, so five CTAs fit an SM instead of four).
-template <class ThrT>
-struct TileTables {
-  static constexpr int kTops = sizeof(ThrT) == 4 ? kThrHiWords : kThrHi16;
-  static constexpr uint32_t kBytes = (uint32_t)sizeof(ThrT) * kTops + 8u * kMoveN;
-  static_assert(kBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
-};
+// The lattice's threshold levels and the move table, contiguous in device
+// memory (thrT, trans), staged with one bulk copy.
+constexpr uint32_t kStagedTableBytes = 2u * kThrT + 8u * kMoveN;
+static_assert(kStagedTableBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 
 // Row band: R rows of one class starting at row j0 + dy of the tile's first a
 // row j0 (periodic in Cy).
@@ -444,10 +429,10 @@ struct Band {
 
 // kBufs: band buffers (three for the pipelined tile loop, one for a CTA that
 // takes a single tile).
-template <class ThrT, int kBufs = kTileBufs>
+template <int kBufs = kTileBufs>
 struct TileSmem {
-  alignas(128) ThrT thrhi[TileTables<ThrT>::kTops];
-  uint2 trans[kMoveN];  // directly after thrhi, as in device memory
+  alignas(128) uint16_t thrT[kThrT];
+  uint2 trans[kMoveN];  // directly after thrT, as in device memory
   alignas(128) uint32_t band[kBufs][kBands][kTileWords];
   alignas(8) unsigned long long full[kBufs];  // bands landed (transaction count)
   alignas(8) unsigned long long tables;       // the tables landed
@@ -517,17 +502,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // One tile-staged phase of lattice g by CTA `cta` of the `ncta` CTAs that
 // work on it; keys: the source of its Philox keys.
 // kSingle: every CTA takes at most one tile (ncta == tiles): one band buffer.
-template <class ThrT, bool kSingle, class Keys>
-__device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
+template <bool kSingle, class Keys>
+__device__ __forceinline__ void tile_phase(const Geo &g, const uint16_t *thrT,
                                            const uint32_t *thr32, int64_t p_off, int cta,
                                            int ncta, const Keys &keys) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
   constexpr int kBufs = kSingle ? 1 : kTileBufs;
-  using Smem = TileSmem<ThrT, kBufs>;
-  constexpr uint32_t kStagedTableBytes = TileTables<ThrT>::kBytes;
+  using Smem = TileSmem<kBufs>;
   Smem &sm = *reinterpret_cast<Smem *>(tile_smem);
-  static_assert(offsetof(Smem, trans) == sizeof(ThrT) * TileTables<ThrT>::kTops,
-                "tables staged as one block");
+  static_assert(offsetof(Smem, trans) == 2 * kThrT, "tables staged as one block");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     sm.err = 0;
@@ -542,7 +525,7 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
     // their copy may start before the previous kernel of the stream finishes.
     const uint32_t bar = smem_u32(&sm.tables);
     mbar_expect(bar, kStagedTableBytes);
-    bulk_load(smem_u32(sm.thrhi), thrhi, kStagedTableBytes, bar);
+    bulk_load(smem_u32(sm.thrT), thrT, kStagedTableBytes, bar);
   }
   // The phase index.  A launch after the first of a chain (p_off > 0) reads the
   // counter base before it waits for its predecessor: the base was written by
@@ -673,7 +656,7 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
     }
     const int tile = sm.tile[b];
     if (tile < 0) break;
-    phase_word<kRowTile>(g, local_u(b), sm.trans, sm.thrhi, thr32, tile * R + jr, jr, w, P,
+    phase_word<kRowTile>(g, local_u(b), sm.trans, sm.thrT, thr32, tile * R + jr, jr, w, P,
                          near128, keys);
     // (2) this warp is done with the tile: its shared-memory writes are ordered
     // before the async copies that will refill the buffer, and before the
@@ -741,17 +724,15 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const ThrT *thrhi,
   }
 }
 
-// ThrT, kMinBlocks, kSingle: uint32_t tops at four CTAs per SM with the
-// pipelined tile loop (the large-lattice kernel: no register spills), or
-// uint16_t tops at five CTAs per SM, one tile per CTA and one band buffer (the
-// compact kernel for lattices whose phase fits one wave: more CTAs resident
-// for several lattices on their own streams, at 48 registers).
-template <class ThrT, int kMinBlocks, bool kSingle>
+// kMinBlocks, kSingle: four CTAs per SM with the pipelined tile loop (the
+// large-lattice kernel), or five CTAs per SM, one tile per CTA and one band
+// buffer (the compact kernel for lattices whose phase fits one wave: more CTAs
+// resident for several lattices on their own streams, at 48 registers).
+template <int kMinBlocks, bool kSingle>
 __global__ void __launch_bounds__(256, kMinBlocks) phase_tile_kernel(
-    Geo g, const ThrT *thrhi, const uint32_t *thr32, int64_t p_off,
+    Geo g, const uint16_t *thrT, const uint32_t *thr32, int64_t p_off,
     const __grid_constant__ RoundKeys rk) {
-  tile_phase<ThrT, kSingle>(g, thrhi, thr32, p_off, (int)blockIdx.x, (int)gridDim.x,
-                            TableKeys{&rk});
+  tile_phase<kSingle>(g, thrT, thr32, p_off, (int)blockIdx.x, (int)gridDim.x, TableKeys{&rk});
 }
 
 // Lock-step tile-staged phase of several lattices in one launch: CTAs
@@ -763,8 +744,8 @@ __global__ void __launch_bounds__(256, 4) phase_tile_multi_kernel(const MultiJob
   while (j + 1 < njobs && (int)blockIdx.x >= jobs[j + 1].cta_begin) ++j;
   const MultiJob &J = jobs[j];
   const Geo g = J.g;
-  tile_phase<uint32_t, false>(g, J.thrhi, J.thr32, p_off, (int)blockIdx.x - J.cta_begin,
-                              J.cta_count, SeedKeys{g.k0, g.k1});
+  tile_phase<false>(g, J.thrT, J.thr32, p_off, (int)blockIdx.x - J.cta_begin, J.cta_count,
+                    SeedKeys{g.k0, g.k1});
 }
 
 // Lock-step phase of several lattices in one launch: each CTA works on one
@@ -783,7 +764,8 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
   __syncthreads();
   const MultiJob &J = jobs[s_job];
   const Geo g = J.g;
-  for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) sm.thrhi[t] = J.thrhi[t];
+  for (int t = threadIdx.x; t < kThrT / 2; t += blockDim.x)
+    reinterpret_cast<uint32_t *>(sm.thrT)[t] = reinterpret_cast<const uint32_t *>(J.thrT)[t];
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
   const uint64_t P = (uint64_t)(g.ctl[kCtlPhaseBase] + p_off);
@@ -804,135 +786,13 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
   int j = wid / g.W, w = wid - j * g.W;
   const int sj = stride / g.W, sw = stride - sj * g.W;
   for (; wid < nw; wid += stride) {
-    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrhi, J.thr32, j, j, w,
+    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrT, J.thr32, j, j, w,
                                                       P, near128, SeedKeys{g.k0, g.k1});
     w += sw;
     j += sj;
     if (w >= g.W) {
       w -= g.W;
       ++j;
-    }
-  }
-}
-
-// ============================================================================
-// One group of phase_word: the pairs 4 b .. 4 b + 3 of a-word w (the four
-// pairs of one Philox call), for the resident kernel on lattices with at most a
-// quarter as many a-words a phase as threads.  Four threads then share a word,
-// each running a quarter of its pairs, which shortens the per-phase chain that
-// bounds such small lattices.  The random streams, fast and exact decisions are
-// phase_word's, so the results are identical; the a word is shared by the four
-// threads, so it is updated by XOR.  kMode: kRowAligned or kRowGeneral.
-template <int kMode>
-__device__ __forceinline__ void phase_group(const Geo &g, const PhaseU &u, const uint2 *trans,
-                                            const uint32_t *thrhi, const uint32_t *thr32, int j,
-                                            int w, int b, uint64_t P, uint32_t near128) {
-  static_assert(kMode != kRowTile, "rows of global or resident memory only");
-  constexpr bool kAligned = kMode != kRowGeneral;
-  const int s0 = w << 4;
-  const int n = kAligned ? 16 : min(16, g.Cx - s0);
-  const int nv = min(4, n - 4 * b);  // pairs of the group inside the row
-  if (nv <= 0) return;
-
-  // ---- gather, pair states and group lanes as in phase_word
-  uint32_t *rowA = const_cast<uint32_t *>(u.cA) + j * g.W;
-  const uint32_t A = rowA[w];
-  const int jb = wrap(j + u.qy, g.Cy);
-  const uint32_t B = window<kMode>(u.cB, g, u, jb, w, u.offB, n);
-  const Sums sa = neighbour_sums(window<kMode>(u.cAL, g, u, j, w, u.offAL, n),
-                                 window<kMode>(u.cAR, g, u, j, w, u.offAR, n),
-                                 u.cAU[wrap(j + u.dyAU, g.Cy) * g.W + w],
-                                 u.cAD[wrap(j + u.dyAD, g.Cy) * g.W + w]);
-  const Sums sb = neighbour_sums(window<kMode>(u.cBL, g, u, jb, w, u.offBL, n),
-                                 window<kMode>(u.cBR, g, u, jb, w, u.offBR, n),
-                                 window<kMode>(u.cBU, g, u, wrap(jb + u.dyBU, g.Cy), w, u.offB, n),
-                                 window<kMode>(u.cBD, g, u, wrap(jb + u.dyBD, g.Cy), w, u.offB, n));
-  const uint32_t pcE = ((A & 0x33333333u) << 2) | (B & 0x33333333u);
-  const uint32_t pcO = (A & 0xCCCCCCCCu) | ((B >> 2) & 0x33333333u);
-  GroupEnv ge;
-  uint32_t pck[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t d8 = group_bytes(sa.se, sa.so, k) + 0x08080808u - group_bytes(sb.se, sb.so, k);
-    const uint32_t ga = group_bytes(sa.ge, sa.go, k);
-    ge.gb[k] = group_bytes(sb.ge, sb.go, k);
-    ge.x01[k] = prmt(d8, ga, 0x5140u);
-    ge.x23[k] = prmt(d8, ga, 0x7362u);
-    pck[k] = group_bytes(pcE, pcO, k) * 8u + near128 * 0x01010101u;
-  }
-
-  // ---- the group's four pairs (pair_env's selector for a run-time b)
-  const uint32_t gbase = (uint32_t)j * (uint32_t)g.Cx4 + (uint32_t)(4 * w);
-  const uint32_t env_sel = 0x8410u + ((b & 1) ? 0x0122u : 0u) + ((b & 2) ? 0x0200u : 0u);
-  const U4 r = philox(gbase + (uint32_t)b, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
-  uint32_t accE = 0u, accO = 0u;
-  uint32_t mn = 0xFFFFFFFFu, mx = 0u, d0 = 0xFFFFFFFFu, v0 = 0u;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (!kAligned && k >= nv) {
-      if (k & 1) {
-        mn = min(mn, d0);
-        mx = max(mx, v0);
-      }
-      continue;
-    }
-    const uint32_t R = k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w;
-    const uint32_t env = prmt(b < 2 ? ge.x01[k] : ge.x23[k], ge.gb[k], env_sel);
-    const uint32_t pc8 = prmt(pck[k], 0u, 0x4440u + (uint32_t)b);
-    const uint32_t v = R & 0xFFFFu;
-    const uint2 e = move_entry(trans, mod12(v), pc8);
-    const uint32_t TH = thr_top(thrhi, __dp4a((int)e.y, (int)env, (int)e.x));
-    const uint32_t d = R - TH;
-    if (k & 1) {
-      mn = __vimin3_u32(mn, d0, d);
-      mx = __vimax3_u32(mx, v0, v);
-    } else {
-      d0 = d;
-      v0 = v;
-    }
-    const uint32_t xm = R < TH ? (e.y & 0xF0000000u) : 0u;
-    if (k & 1)
-      accO = (accO >> 4) | xm;
-    else
-      accE = (accE >> 4) | xm;
-  }
-  const uint32_t slow = (mn < 0x10000u || mx >= 65532u) ? 0xFu << (4 * b) : 0u;
-  // the group's even pairs 4b, 4b+2 (odd 4b+1, 4b+3) belong in lanes 2b, 2b+1
-  // of accE (accO); the pe (po) shifted in sit in the top lanes
-  const int pe = (nv + 1) >> 1, po = nv >> 1;
-  accE >>= 4 * (8 - pe - 2 * b);
-  accO = po == 0 ? 0u : accO >> (4 * (8 - po - 2 * b));
-  uint32_t dA = ((accE >> 2) & 0x33333333u) | (((accO >> 2) & 0x33333333u) << 2);
-  uint32_t dB = (accE & 0x33333333u) | ((accO & 0x33333333u) << 2);
-  if (slow) {
-    const uint2 dd = exact_path<kAligned>(trans, thrhi, thr32, g.k0, g.k1, gbase,
-                                          (uint32_t)((uint64_t)j * g.Cx + s0), n, P, near128, A,
-                                          B, sa, sb, slow, dA, dB);
-    dA = dd.x;
-    dB = dd.y;
-  }
-  if constexpr (!kAligned) {
-    if (n < 16) {
-      const uint32_t valid = (1u << (2 * n)) - 1u;
-      dA &= valid;
-      dB &= valid;
-    }
-  }
-
-  // ---- write back: the a word is shared with the word's other groups
-  if (dA) atomicXor(rowA + w, dA);
-  if (dB) {
-    uint32_t *rb = const_cast<uint32_t *>(u.cB) + jb * g.W;
-    if constexpr (kAligned) {
-      const int wl = wrap(w + (u.offB >> 4), g.W);
-      const int sh = 2 * (u.offB & 15);
-      atomicXor(rb + wl, dB << sh);
-      if (sh) {
-        const uint32_t hi = dB >> (32 - sh);
-        if (hi) atomicXor(rb + (wl + 1 == g.W ? 0 : wl + 1), hi);
-      }
-    } else {
-      scatter_xor(rb, g.Cx, wrap(s0 + u.offB, g.Cx), n, dB);
     }
   }
 }
@@ -948,8 +808,8 @@ __device__ __forceinline__ void phase_group(const Geo &g, const PhaseU &u, const
 __global__ void __launch_bounds__(256, 2) resident_kernel(const JobDesc *__restrict__ jobs, int njobs,
                                                        int *queue) {
   extern __shared__ __align__(16) uint32_t dyn[];
-  uint32_t *s_thrhi = dyn;
-  uint2 *s_trans = reinterpret_cast<uint2 *>(dyn + kThrHiWords);
+  uint16_t *s_thrT = reinterpret_cast<uint16_t *>(dyn);
+  uint2 *s_trans = reinterpret_cast<uint2 *>(dyn + kThrT / 2);
   uint32_t *s_words = dyn + kResTableWords;
   __shared__ Sched s_sched[8];  // the schedules of the current sweep's phases
   __shared__ PhaseU s_u[8];     // and their class pointers and offsets
@@ -964,7 +824,8 @@ __global__ void __launch_bounds__(256, 2) resident_kernel(const JobDesc *__restr
     const JobDesc &J = jobs[job];
     const Geo g = J.g;
     const int64_t nw = 16 * g.cstride;
-    for (int t = threadIdx.x; t < kThrHiWords; t += blockDim.x) s_thrhi[t] = J.thrhi[t];
+    for (int t = threadIdx.x; t < kThrT / 2; t += blockDim.x)
+      dyn[t] = reinterpret_cast<const uint32_t *>(J.thrT)[t];
     for (int t = threadIdx.x; t < kMoveN; t += blockDim.x)
       s_trans[t] = make_uint2(J.trans[2 * t], J.trans[2 * t + 1]);
     for (int64_t t = threadIdx.x; t < nw; t += blockDim.x) s_words[t] = g.words[t];
@@ -975,9 +836,11 @@ __global__ void __launch_bounds__(256, 2) resident_kernel(const JobDesc *__restr
     gs.words = s_words;
     const bool aligned = (g.Cx & 15) == 0;
     const int nwa = g.Cy * g.W;  // a-words per phase
-    // four threads a word (one group of four pairs each) when there are threads
-    // enough, otherwise one word a thread
-    const bool grouped = 4 * nwa <= (int)blockDim.x;
+    // threads a word: as given, else the most (four, two) that still take a
+    // phase's words in one pass of the CTA, else one
+    const int tpw = J.tpw > 0 ? J.tpw
+                  : 4 * nwa <= (int)blockDim.x ? 4
+                  : 2 * nwa <= (int)blockDim.x ? 2 : 1;
     // thread 0's copies of the record count and its ring slot: read once per
     // job, so that a record costs no global load on the sweep's critical path
     int64_t obs_cnt = 0, obs_slot = 0;
@@ -1004,24 +867,28 @@ __global__ void __launch_bounds__(256, 2) resident_kernel(const JobDesc *__restr
         const uint64_t P = (uint64_t)(P0 + 8 * s + p);
         const PhaseU &u = s_u[p];  // read from shared memory where used
         const uint32_t near128 = s_sched[p].near ? 128u : 0u;
-        if (grouped) {
-          if ((int)threadIdx.x < 4 * nwa) {
-            const int wid = threadIdx.x >> 2, b = threadIdx.x & 3;
-            const int j = wid / g.W, w = wid - j * g.W;
-            if (aligned)
-              phase_group<kRowAligned>(gs, u, s_trans, s_thrhi, J.thr32, j, w, b, P, near128);
+        for (int i = threadIdx.x; i < tpw * nwa; i += blockDim.x) {
+          const int wid = tpw == 1 ? i : (tpw == 2 ? i >> 1 : i >> 2), sub = i - tpw * wid;
+          const int j = wid / g.W, w = wid - j * g.W;
+          const SeedKeys keys{gs.k0, gs.k1};
+          if (aligned) {
+            if (tpw == 1)
+              phase_word<kRowAligned, 1>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys);
+            else if (tpw == 2)
+              phase_word<kRowAligned, 2>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
+                                         sub);
             else
-              phase_group<kRowGeneral>(gs, u, s_trans, s_thrhi, J.thr32, j, w, b, P, near128);
-          }
-        } else {
-          for (int wid = threadIdx.x; wid < nwa; wid += blockDim.x) {
-            const int j = wid / g.W, w = wid - j * g.W;
-            if (aligned)
-              phase_word<kRowAligned>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128,
-                                      SeedKeys{gs.k0, gs.k1});
+              phase_word<kRowAligned, 4>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
+                                         sub);
+          } else {
+            if (tpw == 1)
+              phase_word<kRowGeneral, 1>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys);
+            else if (tpw == 2)
+              phase_word<kRowGeneral, 2>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
+                                         sub);
             else
-              phase_word<kRowGeneral>(gs, u, s_trans, s_thrhi, J.thr32, j, j, w, P, near128,
-                                      SeedKeys{gs.k0, gs.k1});
+              phase_word<kRowGeneral, 4>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
+                                         sub);
           }
         }
         __syncthreads();
@@ -1111,12 +978,12 @@ int tile_resident_grid() {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  constexpr int bytes = (int)sizeof(TileSmem<uint32_t>);
-  if (cudaFuncSetAttribute(phase_tile_kernel<uint32_t, 4, false>,
+  constexpr int bytes = (int)sizeof(TileSmem<>);
+  if (cudaFuncSetAttribute(phase_tile_kernel<4, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
       cudaFuncSetAttribute(phase_tile_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            bytes) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<uint32_t, 4, false>, 256,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<4, false>, 256,
                                                     bytes) != cudaSuccess ||
       per_sm < 1 || sms < 1) {
     cudaGetLastError();
@@ -1133,10 +1000,10 @@ int tile_resident_grid_small() {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  constexpr int bytes = (int)sizeof(TileSmem<uint16_t, 1>);
-  if (cudaFuncSetAttribute(phase_tile_kernel<uint16_t, kSmallMinB, true>,
+  constexpr int bytes = (int)sizeof(TileSmem<1>);
+  if (cudaFuncSetAttribute(phase_tile_kernel<kSmallMinB, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<uint16_t, kSmallMinB, true>, 256,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<kSmallMinB, true>, 256,
                                                     bytes) != cudaSuccess ||
       per_sm < 1 || sms < 1) {
     cudaGetLastError();
@@ -1150,32 +1017,32 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
   const int64_t nw = (int64_t)g.Cy * g.W;
   if (cfg.tile_grid > 0) {
     const int64_t tiles = nw / kTileWords;
-    if (t.trans != t.thrhi + kThrHiWords || (reinterpret_cast<uintptr_t>(t.thrhi) & 15u) ||
-        reinterpret_cast<const char *>(t.trans16) !=
-            reinterpret_cast<const char *>(t.thrhi16) + 2 * kThrHi16 ||
-        (reinterpret_cast<uintptr_t>(t.thrhi16) & 15u))
-      return cudaErrorInvalidValue;  // the tables must be staged blocks
+    if (reinterpret_cast<const char *>(t.trans) !=
+            reinterpret_cast<const char *>(t.thrT) + 2 * kThrT ||
+        (reinterpret_cast<uintptr_t>(t.thrT) & 15u))
+      return cudaErrorInvalidValue;  // the tables must be one staged block
     // A phase that fits one wave of the compact kernel (one tile per CTA)
     // takes it: measured faster for several such lattices on their own streams.
     if (cfg.tile_grid_small > 0 && tiles <= cfg.tile_grid_small)
-      return launch_pdl_smem(phase_tile_kernel<uint16_t, kSmallMinB, true>, (int)tiles, 256,
-                             sizeof(TileSmem<uint16_t, 1>), s, g, (const uint16_t *)t.thrhi16,
-                             t.thr32, p_off, round_keys(g.k0, g.k1));
+      return launch_pdl_smem(phase_tile_kernel<kSmallMinB, true>, (int)tiles, 256,
+                             sizeof(TileSmem<1>), s, g, (const uint16_t *)t.thrT, t.thr32,
+                             p_off, round_keys(g.k0, g.k1));
     const int grid = (int)(tiles < cfg.tile_grid ? tiles : cfg.tile_grid);
-    return launch_pdl_smem(phase_tile_kernel<uint32_t, 4, false>, grid, 256, sizeof(TileSmem<uint32_t>),
-                           s, g, (const uint32_t *)t.thrhi, t.thr32, p_off,
+    return launch_pdl_smem(phase_tile_kernel<4, false>, grid, 256, sizeof(TileSmem<>),
+                           s, g, (const uint16_t *)t.thrT, t.thr32, p_off,
                            round_keys(g.k0, g.k1));
   }
   const int grid = grid_for(nw, 256, cfg.phase_grid_cap);
-  const uint32_t *thrhi = t.thrhi, *thr32 = t.thr32, *tr = t.trans;
+  const uint16_t *thrT = t.thrT;
+  const uint32_t *thr32 = t.thr32, *tr = t.trans;
   if ((g.Cx & 15) == 0)
-    return launch_pdl(phase_kernel<true>, grid, 256, s, g, thrhi, thr32, tr, p_off);
-  return launch_pdl(phase_kernel<false>, grid, 256, s, g, thrhi, thr32, tr, p_off);
+    return launch_pdl(phase_kernel<true>, grid, 256, s, g, thrT, thr32, tr, p_off);
+  return launch_pdl(phase_kernel<false>, grid, 256, s, g, thrT, thr32, tr, p_off);
 }
 
 cudaError_t launch_phase_tile_multi(const MultiJob *d_jobs, int njobs, int grid, int64_t p_off,
                                     cudaStream_t s) {
-  return launch_pdl_smem(phase_tile_multi_kernel, grid, 256, sizeof(TileSmem<uint32_t>), s,
+  return launch_pdl_smem(phase_tile_multi_kernel, grid, 256, sizeof(TileSmem<>), s,
                          d_jobs, njobs, p_off);
 }
 

@@ -53,8 +53,8 @@ void build_thresholds(double beta, double Delta, double V, double J, uint32_t *t
 // GA = sum_<a> sigma + 4, GB = sum_<b> sigma + 4:
 //   index = base + (41 dS_a) D8 + dsig_a GA + dsig_b GB.
 // Entry (2 r + near) * 16 + pc: word 0 holds base; word 1 the signed byte
-// coefficients (41 dS_a, dsig_a, dsig_b) and, in its top four bits, pc XOR npc
-// (the phase kernel multiplies byte 3 by zero).
+// coefficients (41 dS_a, dsig_a, dsig_b) and, in bits 24-27 (byte 3, which
+// the phase kernel multiplies by zero; bits 28-31 stay clear), pc XOR npc.
 namespace {
 constexpr int kSetN[3] = {4, 6, 4};  // q = +1, 0, -1
 constexpr int kSets[3][6][2] = {
@@ -84,7 +84,7 @@ bool build_transitions(uint32_t *trans) {
       const int near_base = base + kNB * dSa * dSb + dGa * dGb;
       const uint32_t x = (uint32_t)(((ca ^ na) << 2) | (cb ^ nb));
       const uint32_t coef = ((uint32_t)mulS & 0xFFu) | (((uint32_t)dGa & 0xFFu) << 8) |
-                            (((uint32_t)dGb & 0xFFu) << 16) | (x << 28);
+                            (((uint32_t)dGb & 0xFFu) << 16) | (x << 24);
       for (int near = 0; near < 2; ++near) {
         const int e = (2 * r + near) * 16 + pc;
         trans[2 * e] = (uint32_t)(near ? near_base : base);

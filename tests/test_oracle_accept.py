@@ -1,13 +1,20 @@
 """Acceptance frequency of the oracle's pair move against its threshold.
 
 The Metropolis test of Sec. 3.1 accepts an uphill move with probability
-exp(-beta dE); the oracle takes it as u < thr with u a uniform 32-bit word and
+exp(-beta dE); the oracle takes it as a uniform draw below thr / 2^32 with
 thr = floor(2^32 exp(-beta dE)) (thresholds pinned against 50-digit exp
-elsewhere).  u is split: its top half is the pair's random word R >> 16, its
-low half the low 16 bits of the pair's SLOW Philox word.  Two binomial tests
-pin that split: over uniform top halves the acceptance rate is thr / 2^32, and
-with the top half equal to thr's (a tie) it is (thr mod 2^16) / 2^16, which
-only the low half decides.
+elsewhere).  The pair's 16-bit field v carries both the choice and the top
+part of the acceptance draw: below 65532 = 12 x 5461 the choice is v mod 12
+(mod the q-set's size) and w = floor(v / 12), uniform on [0, 5461), is the
+draw's top part, the pair's SLOW word 0 its low part: accept iff
+w 2^32 + s0 < 5461 thr.  From 65532 up the choice comes from SLOW word 1 and
+the draw is SLOW word 0 alone.  Binomial tests pin each region:
+
+* over uniform w the rate is thr / 2^32;
+* w below T = floor(5461 thr / 2^32) always accepts, above it never does;
+* at w = T (a tie) the rate is the fraction (5461 thr mod 2^32) / 2^32 that
+  only the SLOW word decides;
+* for v >= 65532 the rate is again thr / 2^32, drawn from SLOW word 0.
 """
 import numpy as np
 
@@ -15,6 +22,7 @@ import oracle
 
 A, B = 0, 5  # (0, 0) and (1, 1) of a 4x4 torus: diagonal, no shared bond
 BETA, DELTA, V, J = 0.7, 0.0, 1.0, 1.0
+CHOICE = 2  # choice class 2 of the q = +1 set moves the charge from A to B
 
 
 def _setup():
@@ -25,9 +33,9 @@ def _setup():
     st.flat[9] = 1  # the fourth: sigma = -1
     table = oracle.threshold_table(BETA, DELTA, V, J)
     key = oracle.seed_key(11)
-    # choice class 2 of the q = +1 set moves the charge from A to B
     y = st.copy()
-    assert oracle.pair_move(y, A, B, 2, key, np.zeros(4, np.uint32), np.full_like(table, ~np.uint32(0)))
+    assert oracle.pair_move(y, A, B, CHOICE, key, np.zeros(4, np.uint32),
+                            np.full_like(table, ~np.uint32(0)))
     assert y.flat[A] == 0 and y.flat[B] == 2
     d = oracle.pair_delta(st, A, B, 0, 2)
     # dBV = -2 + 3, dBJ = 2 + 1 (unequal, so that swapped roles would show):
@@ -37,12 +45,15 @@ def _setup():
     return st, table, key, thr
 
 
-def _rate(st, table, key, top_halves):
+def _slow_ctr(i):
+    return np.array([i, 0x5A5A, 3, oracle.TAG_SLOW], np.uint32)
+
+
+def _rate(st, table, key, fields):
     k = 0
-    for i, uh in enumerate(top_halves):
+    for i, v in enumerate(fields):
         x = st.copy()
-        k += oracle.pair_move(x, A, B, 2 | (int(uh) << 16), key,
-                              np.array([i, 0x5A5A, 3, 0x51], np.uint32), table)
+        k += oracle.pair_move(x, A, B, int(v), key, _slow_ctr(i), table)
     return k
 
 
@@ -55,15 +66,46 @@ def test_acceptance_rate_is_threshold_over_two_to_the_32():
     p = thr / 2.0 ** 32
     assert abs(p - np.exp(-BETA * 1.75)) < 2.0 ** -31
     n = 60000
-    top = np.random.default_rng(5).integers(0, 1 << 16, size=n)
-    k = _rate(st, table, key, top)
+    w = np.random.default_rng(5).integers(0, 5461, size=n)
+    k = _rate(st, table, key, 12 * w + CHOICE)
     assert _binomial_ok(k, n, p), (k, n * p)
 
 
-def test_ties_of_the_top_half_are_decided_by_the_low_half():
+def test_draws_below_and_above_the_tie_are_decided_by_the_field_alone():
     st, table, key, thr = _setup()
-    p = (thr & 0xFFFF) / 65536.0
+    T = (5461 * thr) >> 32
+    assert 10 < T < 5450
+    below = [T - 1, T - 2, T // 2, 0]
+    above = [T + 1, T + 2, (T + 5461) // 2, 5460]
+    for w in below:
+        assert _rate(st, table, key, [12 * w + CHOICE] * 200) == 200, w
+    for w in above:
+        assert _rate(st, table, key, [12 * w + CHOICE] * 200) == 0, w
+
+
+def test_ties_are_decided_by_the_slow_word():
+    st, table, key, thr = _setup()
+    T = (5461 * thr) >> 32
+    p = ((5461 * thr) - (T << 32)) / 2.0 ** 32
     assert 0.05 < p < 0.95  # an informative tie for these parameters
     n = 20000
-    k = _rate(st, table, key, np.full(n, thr >> 16))
+    k = _rate(st, table, key, [12 * T + CHOICE] * n)
+    assert _binomial_ok(k, n, p), (k, n * p)
+
+
+def test_fields_from_65532_up_draw_choice_and_acceptance_from_the_slow_words():
+    st, table, key, thr = _setup()
+    p = thr / 2.0 ** 32
+    n, k = 0, 0
+    for i in range(40000):
+        s = oracle.philox(_slow_ctr(i), key)
+        x = st.copy()
+        moved = oracle.pair_move(x, A, B, 65532 + i % 4, key, _slow_ctr(i), table)
+        if int(s[1]) < 4294967292 and int(s[1]) % 4 == CHOICE:
+            n += 1
+            k += moved
+        else:
+            # another choice class: the charge stays, or goes with the other sign
+            assert not (x.flat[A] == 0 and x.flat[B] == 2)
+    assert 9000 < n < 11000  # choice class CHOICE drawn from word 1 a quarter of the time
     assert _binomial_ok(k, n, p), (k, n * p)
