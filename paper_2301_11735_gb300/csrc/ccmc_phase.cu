@@ -152,27 +152,65 @@ __device__ __forceinline__ uint32_t lane_env(const Group &gr, int q) {
                 : prmt(gr.x23, gr.gb, 0x8732u);
 }
 
-// The pairs of a word one thread evaluates: kTPW threads share a word (1, 2 or
-// 4), thread `sub` of them takes MOVE call(s) and half(s):
+// The inputs of a word's pairs: its a word, its b window and the neighbour
+// sums of both sides.
+struct WordIn {
+  uint32_t A, B;
+  Sums sa, sb;
+};
+
+// Row jr + dy of a class (periodic in Cy); staged bands start at the right row.
+template <int kMode>
+__device__ __forceinline__ int band_row(const Geo &g, int r0, int dy) {
+  return kMode == kRowTile ? r0 : wrap(r0 + dy, g.Cy);
+}
+
+// n: the word's sites inside its row (16 unless the row ends in it).
+template <int kMode>
+__device__ __forceinline__ WordIn gather(const Geo &g, const PhaseU &u, int jr, int w, int n) {
+  WordIn in;
+  in.A = u.cA[jr * g.W + w];
+  const int jb = band_row<kMode>(g, jr, u.qy);
+  in.B = window<kMode>(u.cB, g, u, jb, w, u.offB, n);
+  in.sa = neighbour_sums(window<kMode>(u.cAL, g, u, jr, w, u.offAL, n),
+                         window<kMode>(u.cAR, g, u, jr, w, u.offAR, n),
+                         u.cAU[band_row<kMode>(g, jr, u.dyAU) * g.W + w],
+                         u.cAD[band_row<kMode>(g, jr, u.dyAD) * g.W + w]);
+  in.sb = neighbour_sums(window<kMode>(u.cBL, g, u, jb, w, u.offBL, n),
+                         window<kMode>(u.cBR, g, u, jb, w, u.offBR, n),
+                         window<kMode>(u.cBU, g, u, band_row<kMode>(g, jb, u.dyBU), w, u.offB, n),
+                         window<kMode>(u.cBD, g, u, band_row<kMode>(g, jb, u.dyBD), w, u.offB, n));
+  return in;
+}
+
+__device__ __forceinline__ uint32_t pcE_of(const WordIn &in) {
+  return ((in.A & 0x33333333u) << 2) | (in.B & 0x33333333u);
+}
+__device__ __forceinline__ uint32_t pcO_of(const WordIn &in) {
+  return (in.A & 0xCCCCCCCCu) | ((in.B >> 2) & 0x33333333u);
+}
+
+// The fast path of the pairs of a word one thread evaluates: kTPW threads
+// share a word (1, 2 or 4), thread `sub` of them takes MOVE call(s) and
+// half(s):
 //   kTPW 1: both calls, both halves (all 16 pairs);
 //   kTPW 2: call sub, both halves (8 pairs);
 //   kTPW 4: call sub / 2, half sub mod 2 (4 pairs: group k = sub).
-// Returns the word's (dA, dB) contribution of those pairs.
-template <int kMode, int kTPW, class Keys>
-__device__ __forceinline__ uint2 word_moves(const Geo &g, const uint2 *trans,
-                                            const uint16_t *thrT, const uint32_t *thr32, int j,
-                                            int w, int sub, uint32_t A, uint32_t B,
-                                            const Sums &sa, const Sums &sb, uint64_t P,
-                                            uint32_t near128, const Keys &keys) {
+// Returns the (dA, dB) of the fast decisions and, in z, bit c for every call
+// c with a rare pair (a tie or a field >= 65532; the fast path rejected it).
+template <int kTPW, class Keys>
+__device__ __forceinline__ uint3 fast_moves(const Geo &g, const uint2 *trans,
+                                            const uint16_t *thrT, int j, int w, int sub,
+                                            const WordIn &in, uint64_t P, uint32_t near128,
+                                            const Keys &keys) {
   static_assert(kTPW == 1 || kTPW == 2 || kTPW == 4, "one, two or four threads a word");
   constexpr int kCalls = kTPW == 1 ? 2 : 1;
   constexpr int kHalves = kTPW == 4 ? 1 : 2;
   const int c0 = kTPW == 1 ? 0 : (kTPW == 2 ? sub : sub >> 1);
   const int h0 = kTPW == 4 ? (sub & 1) : 0;
-  const uint32_t pcE = ((A & 0x33333333u) << 2) | (B & 0x33333333u);
-  const uint32_t pcO = (A & 0xCCCCCCCCu) | ((B >> 2) & 0x33333333u);
+  const uint32_t pcE = pcE_of(in), pcO = pcO_of(in);
   const uint32_t gbase = (uint32_t)j * (uint32_t)(2 * g.W) + (uint32_t)(2 * w);
-  uint32_t dA = 0u, dB = 0u, slow = 0u;  // slow, bit c: call c needs the exact path
+  uint32_t dA = 0u, dB = 0u, slow = 0u;
 #pragma unroll
   for (int ci = 0; ci < kCalls; ++ci) {
     const int c = c0 + ci;
@@ -182,7 +220,7 @@ __device__ __forceinline__ uint2 word_moves(const Geo &g, const uint2 *trans,
     for (int hi = 0; hi < kHalves; ++hi) {
       const int h = h0 + hi;
       const int k = 2 * c + h;
-      const Group gr = group_env(sa, sb, pcE, pcO, near128, k);
+      const Group gr = group_env(in.sa, in.sb, pcE, pcO, near128, k);
       uint32_t acc = 0u;  // byte q: the accepted move of lane q
       uint32_t d0 = 0xFFFFFFFFu, v0 = 0u;
 #pragma unroll
@@ -203,112 +241,86 @@ __device__ __forceinline__ uint2 word_moves(const Geo &g, const uint2 *trans,
         acc = __funnelshift_l((int)d < 0 ? e.y : 0u, acc, 8);
       }
       // byte q of acc -> site k + 4 q: b bits to 2 (k + 4 q) of dB, a bits of dA
-      const uint32_t bpart = acc & 0x03030303u, apart = (acc >> 2) & 0x03030303u;
-      dB |= bpart << (2 * k);
-      dA |= apart << (2 * k);
+      dB |= (acc & 0x03030303u) << (2 * k);
+      dA |= ((acc >> 2) & 0x03030303u) << (2 * k);
     }
     if (mn == 0u || mx >= 65532u) slow |= 1u << c;
   }
+  return make_uint3(dA, dB, slow);
+}
 
-  // ---- exact path for the flagged calls (a tie or a field >= 65532)
-  if (slow) {
-    const uint32_t slow0 = (uint32_t)((uint64_t)j * g.Cx + (uint32_t)(w << 4));
+// The exact decisions of the rare pairs of MOVE call c of a word (halves h0
+// .. h0 + nh - 1), which the fast path rejected: each decided with its SLOW
+// words by the rule of the random-field reading.  Returns the (dA, dB) of the
+// accepted ones.
+__device__ __forceinline__ uint2 exact_call(const Geo &g, const uint2 *trans,
+                                            const uint16_t *thrT, const uint32_t *thr32, int j,
+                                            int w, int c, int h0, int nh, const WordIn &in,
+                                            uint64_t P, uint32_t near128) {
+  const uint32_t pcE = pcE_of(in), pcO = pcO_of(in);
+  const uint32_t gbase = (uint32_t)j * (uint32_t)(2 * g.W) + (uint32_t)(2 * w);
+  const uint32_t slow0 = (uint32_t)((uint64_t)j * g.Cx + (uint32_t)(w << 4));
+  const U4 r = philox(gbase + (uint32_t)c, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
+  uint32_t dA = 0u, dB = 0u;
 #pragma unroll 1
-    for (int ci = 0; ci < kCalls; ++ci) {
-      const int c = c0 + ci;
-      if (!((slow >> c) & 1u)) continue;
-      const U4 r = philox(gbase + (uint32_t)c, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0,
-                          g.k1);
+  for (int h = h0; h < h0 + nh; ++h) {
+    const int k = 2 * c + h;
+    const Group gr = group_env(in.sa, in.sb, pcE, pcO, near128, k);
 #pragma unroll 1
-      for (int hi = 0; hi < kHalves; ++hi) {
-        const int h = h0 + hi;
-        const int k = 2 * c + h;
-        const Group gr = group_env(sa, sb, pcE, pcO, near128, k);
-#pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t X = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
-          const uint32_t v = h ? X >> 16 : X & 0xFFFFu;
-          const uint32_t wq = div12(v);
-          const uint32_t pc8 = prmt(gr.pc8, 0u, 0x4440u + (uint32_t)q);
-          const uint32_t env = prmt(q < 2 ? gr.x01 : gr.x23, gr.gb,
-                                    0x8410u + ((q & 1) ? 0x0122u : 0u) + ((q & 2) ? 0x0200u : 0u));
-          const uint2 ef = move_entry(trans, v - 12u * wq, pc8);
-          if (v < 65532u && wq != thrT[__dp4a((int)ef.y, (int)env, (int)ef.x)]) continue;
-          // a rare pair: the fast path rejected it; decide it exactly
-          const int t = k + 4 * q;
-          const U4 sl = philox(slow0 + (uint32_t)t, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW,
-                               g.k0, g.k1);
-          uint2 e = ef;
-          if (v >= 65532u) {
-            if (sl.y >= 4294967292u) continue;  // keep the current configuration
-            e = move_entry(trans, sl.y % 12u, pc8);
-          }
-          const uint32_t thr = thr32[__dp4a((int)e.y, (int)env, (int)e.x)];
-          const bool accept =
-              thr == 0xFFFFFFFFu ||
-              (v < 65532u ? ((uint64_t)wq << 32) + sl.x < 5461ull * thr : sl.x < thr);
-          if (accept) {
-            const uint32_t x = move_nibble(e.y);
-            dA ^= (x >> 2) << (2 * t);
-            dB ^= (x & 3u) << (2 * t);
-          }
-        }
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t X = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
+      const uint32_t v = h ? X >> 16 : X & 0xFFFFu;
+      const uint32_t wq = div12(v);
+      const uint32_t pc8 = prmt(gr.pc8, 0u, 0x4440u + (uint32_t)q);
+      const uint32_t env = prmt(q < 2 ? gr.x01 : gr.x23, gr.gb,
+                                0x8410u + ((q & 1) ? 0x0122u : 0u) + ((q & 2) ? 0x0200u : 0u));
+      const uint2 ef = move_entry(trans, v - 12u * wq, pc8);
+      if (v < 65532u && wq != thrT[__dp4a((int)ef.y, (int)env, (int)ef.x)]) continue;
+      const int t = k + 4 * q;
+      const U4 sl = philox(slow0 + (uint32_t)t, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW,
+                           g.k0, g.k1);
+      uint2 e = ef;
+      if (v >= 65532u) {
+        if (sl.y >= 4294967292u) continue;  // keep the current configuration
+        e = move_entry(trans, sl.y % 12u, pc8);
+      }
+      const uint32_t thr = thr32[__dp4a((int)e.y, (int)env, (int)e.x)];
+      const bool accept =
+          thr == 0xFFFFFFFFu ||
+          (v < 65532u ? ((uint64_t)wq << 32) + sl.x < 5461ull * thr : sl.x < thr);
+      if (accept) {
+        const uint32_t x = move_nibble(e.y);
+        dA ^= (x >> 2) << (2 * t);
+        dB ^= (x & 3u) << (2 * t);
       }
     }
   }
   return make_uint2(dA, dB);
 }
 
-// j: the pair's row in the class (keys the random streams); jr: the row of the
-// a word in u's arrays (j itself for the lattice in global memory, the row
-// inside a staged tile otherwise); near128: 128 if the phase's partners are
-// nearest neighbours, else 0; keys: the source of the Philox keys (SeedKeys or
-// TableKeys of the lattice's seed); kTPW threads share the word, this one is
-// thread `sub` of them (see word_moves).
-template <int kMode, int kTPW = 1, class Keys = SeedKeys>
-__device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
-                                           const uint16_t *thrT, const uint32_t *thr32, int j,
-                                           int jr, int w, uint64_t P, uint32_t near128,
-                                           const Keys &keys, int sub = 0) {
-  constexpr bool kAligned = kMode != kRowGeneral;
-  // row jr + dy of a class (periodic in Cy); staged bands start at the right row
-  auto row = [&](int r0, int dy) { return kMode == kRowTile ? r0 : wrap(r0 + dy, g.Cy); };
-  const int s0 = w << 4;
-  const int n = kAligned ? 16 : min(16, g.Cx - s0);
-
-  // ---- gather: the a word, the b window and the eight neighbour windows
-  uint32_t *rowA = const_cast<uint32_t *>(u.cA) + jr * g.W;
-  const uint32_t A = rowA[w];
-  const int jb = row(jr, u.qy);
-  const uint32_t B = window<kMode>(u.cB, g, u, jb, w, u.offB, n);
-  const Sums sa = neighbour_sums(window<kMode>(u.cAL, g, u, jr, w, u.offAL, n),
-                                 window<kMode>(u.cAR, g, u, jr, w, u.offAR, n),
-                                 u.cAU[row(jr, u.dyAU) * g.W + w], u.cAD[row(jr, u.dyAD) * g.W + w]);
-  const Sums sb = neighbour_sums(window<kMode>(u.cBL, g, u, jb, w, u.offBL, n),
-                                 window<kMode>(u.cBR, g, u, jb, w, u.offBR, n),
-                                 window<kMode>(u.cBU, g, u, row(jb, u.dyBU), w, u.offB, n),
-                                 window<kMode>(u.cBD, g, u, row(jb, u.dyBD), w, u.offB, n));
-  const uint2 d = word_moves<kMode, kTPW>(g, trans, thrT, thr32, j, w, sub, A, B, sa, sb, P,
-                                          near128, keys);
-  uint32_t dA = d.x, dB = d.y;
-  if constexpr (!kAligned) {
+// Apply the moves (dA, dB) of word w (row jr of u's arrays, n sites): the a
+// word by a plain read-modify-write when this thread owns it (kOwnA), else by
+// atomic XOR; the b sites by atomic XOR (their words are shared with the
+// partners of neighbouring words).
+template <int kMode, bool kOwnA>
+__device__ __forceinline__ void apply_moves(const Geo &g, const PhaseU &u, int jr, int w, int n,
+                                            uint32_t dA, uint32_t dB) {
+  if constexpr (kMode == kRowGeneral) {
     if (n < 16) {  // pairs past the end of the row do not exist
       const uint32_t valid = (1u << (2 * n)) - 1u;
       dA &= valid;
       dB &= valid;
     }
   }
-
-  // ---- write back: the a word is this thread's alone unless threads share
-  // it; the b sites share words with neighbouring words' partners
   if (dA) {
-    if constexpr (kTPW == 1)
-      rowA[w] = A ^ dA;
+    uint32_t *pa = const_cast<uint32_t *>(u.cA) + jr * g.W + w;
+    if constexpr (kOwnA)
+      *pa ^= dA;
     else
-      atomicXor(rowA + w, dA);
+      atomicXor(pa, dA);
   }
   if (dB) {
-    uint32_t *rb = const_cast<uint32_t *>(u.cB) + jb * g.W;
+    uint32_t *rb = const_cast<uint32_t *>(u.cB) + band_row<kMode>(g, jr, u.qy) * g.W;
     if constexpr (kMode == kRowTile) {
       const int wl = (w + (u.offB >> 4)) & u.wmask;
       const int sh = 2 * (u.offB & 15);
@@ -317,7 +329,7 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
         const uint32_t hi = dB >> (32 - sh);
         if (hi) atomicXor(rb + ((wl + 1) & u.wmask), hi);
       }
-    } else if constexpr (kAligned) {
+    } else if constexpr (kMode == kRowAligned) {
       const int wl = wrap(w + (u.offB >> 4), g.W);
       const int sh = 2 * (u.offB & 15);
       atomicXor(rb + wl, dB << sh);
@@ -326,7 +338,116 @@ __device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const 
         if (hi) atomicXor(rb + (wl + 1 == g.W ? 0 : wl + 1), hi);
       }
     } else {
-      scatter_xor(rb, g.Cx, wrap(s0 + u.offB, g.Cx), n, dB);
+      scatter_xor(rb, g.Cx, wrap((w << 4) + u.offB, g.Cx), n, dB);
+    }
+  }
+}
+
+// One word's pairs, rare ones included (the exact path inline): j the a
+// word's row in the class (keys the random streams), jr its row in u's arrays
+// (j itself for a lattice in global memory, the row inside a staged tile
+// otherwise), near128 128 if the phase's partners are nearest neighbours,
+// keys the source of the Philox keys (SeedKeys or TableKeys of the lattice's
+// seed); kTPW threads share the word, this one is thread `sub` of them.
+template <int kMode, int kTPW = 1, class Keys = SeedKeys>
+__device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
+                                           const uint16_t *thrT, const uint32_t *thr32, int j,
+                                           int jr, int w, uint64_t P, uint32_t near128,
+                                           const Keys &keys, int sub = 0) {
+  const int n = kMode == kRowGeneral ? min(16, g.Cx - (w << 4)) : 16;
+  const WordIn in = gather<kMode>(g, u, jr, w, n);
+  uint3 d = fast_moves<kTPW>(g, trans, thrT, j, w, sub, in, P, near128, keys);
+  if (d.z) {
+    const int h0 = kTPW == 4 ? (sub & 1) : 0, nh = kTPW == 4 ? 1 : 2;
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c)
+      if ((d.z >> c) & 1u) {
+        const uint2 x = exact_call(g, trans, thrT, thr32, j, w, c, h0, nh, in, P, near128);
+        d.x ^= x.x;
+        d.y ^= x.y;
+      }
+  }
+  apply_moves<kMode, kTPW == 1>(g, u, jr, w, n, d.x, d.y);
+}
+
+// The exact path of one pair, by one lane of a warp that takes the rare calls
+// of a word together: pair t = k + 4 q (group k = 2 c + h, lane q of the
+// group) of MOVE call c of word w (inputs `in`), decided with its SLOW words
+// if it is rare (the fast path rejected it), and applied to the word's a and
+// b sites by atomic XOR.
+template <int kMode>
+__device__ __forceinline__ void exact_pair(const Geo &g, const PhaseU &u, const uint2 *trans,
+                                           const uint16_t *thrT, const uint32_t *thr32, int j,
+                                           int jr, int w, int c, int h, int q, const WordIn &in,
+                                           uint64_t P, uint32_t near128) {
+  const int k = 2 * c + h;
+  const uint32_t gbase = (uint32_t)j * (uint32_t)(2 * g.W) + (uint32_t)(2 * w);
+  const U4 r = philox(gbase + (uint32_t)c, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
+  const uint32_t X = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
+  const uint32_t v = h ? X >> 16 : X & 0xFFFFu;
+  const uint32_t wq = div12(v);
+  const Group gr = group_env(in.sa, in.sb, pcE_of(in), pcO_of(in), near128, k);
+  const uint32_t pc8 = prmt(gr.pc8, 0u, 0x4440u + (uint32_t)q);
+  const uint32_t env = prmt(q < 2 ? gr.x01 : gr.x23, gr.gb,
+                            0x8410u + ((q & 1) ? 0x0122u : 0u) + ((q & 2) ? 0x0200u : 0u));
+  uint2 e = move_entry(trans, v - 12u * wq, pc8);
+  if (v < 65532u && wq != thrT[__dp4a((int)e.y, (int)env, (int)e.x)]) return;  // not rare
+  const int t = k + 4 * q;
+  const uint32_t slow0 = (uint32_t)((uint64_t)j * g.Cx + (uint32_t)(w << 4));
+  const U4 sl = philox(slow0 + (uint32_t)t, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, g.k0, g.k1);
+  if (v >= 65532u) {
+    if (sl.y >= 4294967292u) return;  // keep the current configuration
+    e = move_entry(trans, sl.y % 12u, pc8);
+  }
+  const uint32_t thr = thr32[__dp4a((int)e.y, (int)env, (int)e.x)];
+  const bool accept = thr == 0xFFFFFFFFu ||
+                      (v < 65532u ? ((uint64_t)wq << 32) + sl.x < 5461ull * thr : sl.x < thr);
+  if (accept) {
+    const uint32_t x = move_nibble(e.y);
+    apply_moves<kMode, false>(g, u, jr, w, 16, (x >> 2) << (2 * t), (x & 3u) << (2 * t));
+  }
+}
+
+// One word of a staged tile (all 32 lanes of the warp take part, one word
+// each): the fast decisions are applied; then, for every lane with rare calls
+// (about one word in 250), the warp decides that word's rare pairs together,
+// one pair a lane (16 lanes for the two calls), from the owner's inputs.  The
+// rare pairs were rejected by the fast path, and no other pair of the phase
+// touches their sites or neighbours, so the order does not matter.
+template <class Keys>
+__device__ __forceinline__ void tile_word(const Geo &g, const PhaseU &u, const uint2 *trans,
+                                          const uint16_t *thrT, const uint32_t *thr32, int j,
+                                          int jr, int w, uint64_t P, uint32_t near128,
+                                          const Keys &keys) {
+  const WordIn in = gather<kRowTile>(g, u, jr, w, 16);
+  const uint3 d = fast_moves<1>(g, trans, thrT, j, w, 0, in, P, near128, keys);
+  apply_moves<kRowTile, true>(g, u, jr, w, 16, d.x, d.y);
+  unsigned ball = __ballot_sync(0xFFFFFFFFu, d.z != 0u);
+  if (ball) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();  // the fast moves of every lane are in shared memory
+#pragma unroll 1
+    while (ball) {
+      const int src = __ffs(ball) - 1;
+      ball &= ball - 1u;
+      const uint32_t rz = __shfl_sync(0xFFFFFFFFu, d.z, src);
+      WordIn o;
+      o.A = __shfl_sync(0xFFFFFFFFu, in.A, src);
+      o.B = __shfl_sync(0xFFFFFFFFu, in.B, src);
+      o.sa.se = __shfl_sync(0xFFFFFFFFu, in.sa.se, src);
+      o.sa.so = __shfl_sync(0xFFFFFFFFu, in.sa.so, src);
+      o.sa.ge = __shfl_sync(0xFFFFFFFFu, in.sa.ge, src);
+      o.sa.go = __shfl_sync(0xFFFFFFFFu, in.sa.go, src);
+      o.sb.se = __shfl_sync(0xFFFFFFFFu, in.sb.se, src);
+      o.sb.so = __shfl_sync(0xFFFFFFFFu, in.sb.so, src);
+      o.sb.ge = __shfl_sync(0xFFFFFFFFu, in.sb.ge, src);
+      o.sb.go = __shfl_sync(0xFFFFFFFFu, in.sb.go, src);
+      const int oj = __shfl_sync(0xFFFFFFFFu, j, src), ojr = __shfl_sync(0xFFFFFFFFu, jr, src),
+                ow = __shfl_sync(0xFFFFFFFFu, w, src);
+      const int c = (lane >> 3) & 1;
+      if (lane < 16 && ((rz >> c) & 1u))
+        exact_pair<kRowTile>(g, u, trans, thrT, thr32, oj, ojr, ow, c, (lane >> 2) & 1, lane & 3,
+                             o, P, near128);
     }
   }
 }
@@ -656,8 +777,7 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint16_t *thrT,
     }
     const int tile = sm.tile[b];
     if (tile < 0) break;
-    phase_word<kRowTile>(g, local_u(b), sm.trans, sm.thrT, thr32, tile * R + jr, jr, w, P,
-                         near128, keys);
+    tile_word(g, local_u(b), sm.trans, sm.thrT, thr32, tile * R + jr, jr, w, P, near128, keys);
     // (2) this warp is done with the tile: its shared-memory writes are ordered
     // before the async copies that will refill the buffer, and before the
     // last warp's reads
