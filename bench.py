@@ -343,7 +343,7 @@ def measure_batched(cc, nsweeps=5000, plain_per_size=4):
         lat.init_constrained(s.seed, s.n, s.charged_frac)
         lats.append(lat)
     with cc.Batch(lats) as b:
-        cfg = b.autotune(probe_sweeps=10)
+        cfg = b.autotune(probe_sweeps=200)
         b.sweep(3, *cols)
         b.sync()
         torch.cuda.synchronize()
@@ -375,7 +375,8 @@ def measure_batched(cc, nsweeps=5000, plain_per_size=4):
     return {"workload": "512 replicas, L~U{32,64,128,256}, T grid [0.1,3], n~U{0,.1,.2,.3}, "
                         "Delta~U{-.5,0,.5}, V=J=1, 5000 sweeps",
             "value": work / dt, "unit": "site-updates/s", "seconds": dt,
-            "config": {"threads": cfg[0], "resident_max_sites": cfg[1], "ctas_per_sm": cfg[2]},
+            "config": {"threads": cfg[0], "resident_max_sites": cfg[1], "ctas_per_sm": cfg[2],
+                       "max_threads_per_word": cfg[3]},
             "plain_back_to_back": {"value": plain, "unit": "site-updates/s",
                                    "sample": f"{len(picked)} of the lattices ({plain_per_size} of "
                                              f"each size), the full {nsweeps} sweeps each, one "
@@ -409,7 +410,7 @@ def measure_small(cc, reps=3):
             best = min(best, time.perf_counter() - t0)
         out["plain_us_per_sweep"] = 1e6 * best / nsw
         with cc.Batch([lat]) as b:
-            out["batched_config"] = list(b.autotune(probe_sweeps=10))
+            out["batched_config"] = list(b.autotune(probe_sweeps=200))
             cols = ([beta], [c["Delta"]], [c["V"]], [c["J"]])
             b.sweep(20, *cols, obs_every=1)
             b.sync()

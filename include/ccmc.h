@@ -118,10 +118,14 @@ int ccmc_batch_create(int count, ccmc_lattice *const *lattices, void *cuda_strea
                       ccmc_batch **out);
 int ccmc_batch_destroy(ccmc_batch *b);
 /* Launch shape of the resident launch (autotuner knobs; results do not depend
- * on them): threads per CTA (64, 128 or 256), the largest lattice (in sites)
- * kept in shared memory, and CTAs per SM of the persistent grid. */
+ * on them): threads per CTA (64, 128, 256 or 512), the largest lattice (in
+ * sites) kept in shared memory, CTAs per SM of the persistent grid, and the
+ * most threads that share one packed word (16 pairs) of a lattice: 1, 2 or 4
+ * (each lattice takes the most, up to this, that still covers a phase's words
+ * in one pass of its CTA).  Errors: E_INVAL (a value out of range, or a
+ * resident limit beyond the device's shared memory). */
 int ccmc_batch_config(ccmc_batch *b, int resident_threads, int64_t resident_max_sites,
-                      int ctas_per_sm);
+                      int ctas_per_sm, int max_threads_per_word);
 int ccmc_batch_sweep(ccmc_batch *b, const int64_t *nsweeps, const double *beta,
                      const double *Delta, const double *V, const double *J, int obs_every);
 /* Wait for the batch stream and every member's stream; reports device errors. */

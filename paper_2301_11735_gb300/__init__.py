@@ -92,7 +92,7 @@ def _load():
         "ccmc_selftest_wait": (c_int, [c_uint32]),
         "ccmc_batch_create": (c_int, [c_int, POINTER(vp), vp, POINTER(vp)]),
         "ccmc_batch_destroy": (c_int, [vp]),
-        "ccmc_batch_config": (c_int, [vp, c_int, c_int64, c_int]),
+        "ccmc_batch_config": (c_int, [vp, c_int, c_int64, c_int, c_int]),
         "ccmc_batch_sweep": (c_int, [vp, i64p, POINTER(c_double), POINTER(c_double),
                                      POINTER(c_double), POINTER(c_double), c_int]),
         "ccmc_batch_sync": (c_int, [vp]),
@@ -320,9 +320,10 @@ class Batch:
                                        ctypes.byref(h)), "ccmc_batch_create")
         self._h = h
 
-    def config(self, threads: int = 256, resident_max_sites: int = 1 << 17, ctas_per_sm: int = 2):
-        _check(lib().ccmc_batch_config(self._h, threads, resident_max_sites, ctas_per_sm),
-               "ccmc_batch_config")
+    def config(self, threads: int = 256, resident_max_sites: int = 1 << 17, ctas_per_sm: int = 2,
+               max_threads_per_word: int = 4):
+        _check(lib().ccmc_batch_config(self._h, threads, resident_max_sites, ctas_per_sm,
+                                       max_threads_per_word), "ccmc_batch_config")
 
     def autotune(self, probe_sweeps: int = 20):
         """Time the candidate launch shapes on a probe batch of the same shapes

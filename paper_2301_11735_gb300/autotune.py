@@ -1,9 +1,11 @@
 """Autotuner for batched sweeps: picks the launch shape of a batch by timing.
 
-The knobs (ccmc_batch_config) are the threads per CTA of the resident launch,
-its CTAs per SM, and the largest lattice kept in shared memory (the rest take
-the per-phase HBM/L2 path).  None of them changes results -- the random streams
-are keyed by (seed, phase, site) -- so the tuner may pick freely.
+The knobs (ccmc_batch_config) are the threads per CTA of the resident launch
+(64 to 512), its CTAs per SM, the largest lattice kept in shared memory (the
+shared-memory path; the rest take the per-phase L2/HBM path), and the most
+threads that share one packed word of a lattice (1, 2 or 4: the pairs each
+thread evaluates, 16, 8 or 4).  None of them changes results -- the random
+streams are keyed by (seed, phase, site) -- so the tuner may pick freely.
 
 A probe batch of synthetic lattices with the same shapes is swept for a few
 sweeps under every candidate; the fastest candidate is cached in a JSON file
@@ -19,15 +21,17 @@ import time
 
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
-# (threads per CTA, largest resident lattice in sites, CTAs per SM): the
-# argument order of Batch.config
-DEFAULT = (256, 1 << 17, 2)
+# (threads per CTA, largest resident lattice in sites, CTAs per SM, most
+# threads a word): the argument order of Batch.config
+DEFAULT = (256, 1 << 17, 2, 4)
 CANDIDATES = [
-    (threads, resident, ctas)
+    (threads, resident, ctas, tpw)
     for threads in (128, 256)
     for resident in (1 << 12, 1 << 14, 1 << 17)
     for ctas in (2, 4)
-] + [(64, 1 << 17, 2)]
+    for tpw in (1, 4)
+] + [(64, 1 << 17, 2, 4), (256, 1 << 17, 2, 2), (512, 1 << 17, 1, 2), (512, 1 << 17, 1, 4),
+     (512, 1 << 17, 1, 1)]
 
 
 def _gpu_name() -> str:
@@ -67,7 +71,7 @@ def tune(shapes, probe_sweeps: int = 20, params=(1.0, 0.0, 1.0, 1.0), use_cache:
     """Best (threads, resident_max_sites, ctas_per_sm) for a batch of `shapes`."""
     import paper_2301_11735_gb300 as cc
 
-    key = f"{_gpu_name()}|{signature(shapes)}"
+    key = f"{_gpu_name()}|{signature(shapes)}|{len(DEFAULT)}"
     cache = _load() if use_cache else {}
     if key in cache:
         return tuple(cache[key]["config"])

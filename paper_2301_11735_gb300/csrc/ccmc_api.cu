@@ -612,6 +612,7 @@ struct ccmc_batch {
   int threads = 256;
   int64_t resident_max_sites = (int64_t)1 << 18;
   int ctas_per_sm = 2;
+  int max_tpw = 4;
   int sms = 152;
   cudaEvent_t ev = nullptr;
   std::vector<cudaEvent_t> lat_ev;
@@ -787,6 +788,7 @@ int batch_run(ccmc_batch *b, const std::vector<ccmc_lattice *> &lats, const int6
     int rc = upload_params_on(h, beta[i], Delta[i], V[i], J[i], b->stream);
     if (rc) return rc;
     jobs.push_back(job_of(h, nsweeps[i], obs_every[i]));
+    jobs.back().max_tpw = b->max_tpw;
     resident.push_back(i);
   }
   if (!jobs.empty()) {
@@ -948,9 +950,12 @@ int ccmc_batch_destroy(ccmc_batch *b) {
 }
 
 int ccmc_batch_config(ccmc_batch *b, int resident_threads, int64_t resident_max_sites,
-                      int ctas_per_sm) {
+                      int ctas_per_sm, int max_threads_per_word) {
   if (!b) return CCMC_E_INVAL;
-  if (resident_threads != 64 && resident_threads != 128 && resident_threads != 256)
+  if (resident_threads != 64 && resident_threads != 128 && resident_threads != 256 &&
+      resident_threads != 512)
+    return CCMC_E_INVAL;
+  if (max_threads_per_word != 1 && max_threads_per_word != 2 && max_threads_per_word != 4)
     return CCMC_E_INVAL;
   if (resident_max_sites < 0 || ctas_per_sm < 1 || ctas_per_sm > 32) return CCMC_E_INVAL;
   int dev = 0, optin = 0;
@@ -961,6 +966,7 @@ int ccmc_batch_config(ccmc_batch *b, int resident_threads, int64_t resident_max_
   b->threads = resident_threads;
   b->resident_max_sites = resident_max_sites;
   b->ctas_per_sm = ctas_per_sm;
+  b->max_tpw = max_threads_per_word;
   return CCMC_OK;
 }
 

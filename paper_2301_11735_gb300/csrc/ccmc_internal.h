@@ -84,7 +84,8 @@ struct JobDesc {
   int64_t *hist;            // histograms (nullptr: none)
   int nbins;
   int obs_every;
-  int tpw;                  // threads a word: 1, 2 or 4 (0: by the lattice's size)
+  int max_tpw;              // threads a word: the most of 4, 2, 1 (at most max_tpw) that
+                            // take a phase's words in one pass of the CTA, else 1
 };
 
 // One lattice of a lock-step multi-lattice phase launch: CTAs

@@ -249,55 +249,6 @@ __device__ __forceinline__ uint3 fast_moves(const Geo &g, const uint2 *trans,
   return make_uint3(dA, dB, slow);
 }
 
-// The exact decisions of the rare pairs of MOVE call c of a word (halves h0
-// .. h0 + nh - 1), which the fast path rejected: each decided with its SLOW
-// words by the rule of the random-field reading.  Returns the (dA, dB) of the
-// accepted ones.
-__device__ __forceinline__ uint2 exact_call(const Geo &g, const uint2 *trans,
-                                            const uint16_t *thrT, const uint32_t *thr32, int j,
-                                            int w, int c, int h0, int nh, const WordIn &in,
-                                            uint64_t P, uint32_t near128) {
-  const uint32_t pcE = pcE_of(in), pcO = pcO_of(in);
-  const uint32_t gbase = (uint32_t)j * (uint32_t)(2 * g.W) + (uint32_t)(2 * w);
-  const uint32_t slow0 = (uint32_t)((uint64_t)j * g.Cx + (uint32_t)(w << 4));
-  const U4 r = philox(gbase + (uint32_t)c, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
-  uint32_t dA = 0u, dB = 0u;
-#pragma unroll 1
-  for (int h = h0; h < h0 + nh; ++h) {
-    const int k = 2 * c + h;
-    const Group gr = group_env(in.sa, in.sb, pcE, pcO, near128, k);
-#pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t X = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
-      const uint32_t v = h ? X >> 16 : X & 0xFFFFu;
-      const uint32_t wq = div12(v);
-      const uint32_t pc8 = prmt(gr.pc8, 0u, 0x4440u + (uint32_t)q);
-      const uint32_t env = prmt(q < 2 ? gr.x01 : gr.x23, gr.gb,
-                                0x8410u + ((q & 1) ? 0x0122u : 0u) + ((q & 2) ? 0x0200u : 0u));
-      const uint2 ef = move_entry(trans, v - 12u * wq, pc8);
-      if (v < 65532u && wq != thrT[__dp4a((int)ef.y, (int)env, (int)ef.x)]) continue;
-      const int t = k + 4 * q;
-      const U4 sl = philox(slow0 + (uint32_t)t, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW,
-                           g.k0, g.k1);
-      uint2 e = ef;
-      if (v >= 65532u) {
-        if (sl.y >= 4294967292u) continue;  // keep the current configuration
-        e = move_entry(trans, sl.y % 12u, pc8);
-      }
-      const uint32_t thr = thr32[__dp4a((int)e.y, (int)env, (int)e.x)];
-      const bool accept =
-          thr == 0xFFFFFFFFu ||
-          (v < 65532u ? ((uint64_t)wq << 32) + sl.x < 5461ull * thr : sl.x < thr);
-      if (accept) {
-        const uint32_t x = move_nibble(e.y);
-        dA ^= (x >> 2) << (2 * t);
-        dB ^= (x & 3u) << (2 * t);
-      }
-    }
-  }
-  return make_uint2(dA, dB);
-}
-
 // Apply the moves (dA, dB) of word w (row jr of u's arrays, n sites): the a
 // word by a plain read-modify-write when this thread owns it (kOwnA), else by
 // atomic XOR; the b sites by atomic XOR (their words are shared with the
@@ -343,44 +294,19 @@ __device__ __forceinline__ void apply_moves(const Geo &g, const PhaseU &u, int j
   }
 }
 
-// One word's pairs, rare ones included (the exact path inline): j the a
-// word's row in the class (keys the random streams), jr its row in u's arrays
-// (j itself for a lattice in global memory, the row inside a staged tile
-// otherwise), near128 128 if the phase's partners are nearest neighbours,
-// keys the source of the Philox keys (SeedKeys or TableKeys of the lattice's
-// seed); kTPW threads share the word, this one is thread `sub` of them.
-template <int kMode, int kTPW = 1, class Keys = SeedKeys>
-__device__ __forceinline__ void phase_word(const Geo &g, const PhaseU &u, const uint2 *trans,
-                                           const uint16_t *thrT, const uint32_t *thr32, int j,
-                                           int jr, int w, uint64_t P, uint32_t near128,
-                                           const Keys &keys, int sub = 0) {
-  const int n = kMode == kRowGeneral ? min(16, g.Cx - (w << 4)) : 16;
-  const WordIn in = gather<kMode>(g, u, jr, w, n);
-  uint3 d = fast_moves<kTPW>(g, trans, thrT, j, w, sub, in, P, near128, keys);
-  if (d.z) {
-    const int h0 = kTPW == 4 ? (sub & 1) : 0, nh = kTPW == 4 ? 1 : 2;
-#pragma unroll 1
-    for (int c = 0; c < 2; ++c)
-      if ((d.z >> c) & 1u) {
-        const uint2 x = exact_call(g, trans, thrT, thr32, j, w, c, h0, nh, in, P, near128);
-        d.x ^= x.x;
-        d.y ^= x.y;
-      }
-  }
-  apply_moves<kMode, kTPW == 1>(g, u, jr, w, n, d.x, d.y);
-}
-
 // The exact path of one pair, by one lane of a warp that takes the rare calls
 // of a word together: pair t = k + 4 q (group k = 2 c + h, lane q of the
-// group) of MOVE call c of word w (inputs `in`), decided with its SLOW words
-// if it is rare (the fast path rejected it), and applied to the word's a and
-// b sites by atomic XOR.
+// group) of MOVE call c of word w (inputs `in`, n sites in the row), decided
+// with its SLOW words if it is rare (the fast path rejected it), and applied
+// to the word's a and b sites by atomic XOR.
 template <int kMode>
 __device__ __forceinline__ void exact_pair(const Geo &g, const PhaseU &u, const uint2 *trans,
                                            const uint16_t *thrT, const uint32_t *thr32, int j,
-                                           int jr, int w, int c, int h, int q, const WordIn &in,
-                                           uint64_t P, uint32_t near128) {
+                                           int jr, int w, int n, int c, int h, int q,
+                                           const WordIn &in, uint64_t P, uint32_t near128) {
   const int k = 2 * c + h;
+  const int t = k + 4 * q;
+  if (t >= n) return;  // past the end of the row: no pair
   const uint32_t gbase = (uint32_t)j * (uint32_t)(2 * g.W) + (uint32_t)(2 * w);
   const U4 r = philox(gbase + (uint32_t)c, (uint32_t)P, (uint32_t)(P >> 32), TAG_MOVE, g.k0, g.k1);
   const uint32_t X = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
@@ -392,7 +318,6 @@ __device__ __forceinline__ void exact_pair(const Geo &g, const PhaseU &u, const 
                             0x8410u + ((q & 1) ? 0x0122u : 0u) + ((q & 2) ? 0x0200u : 0u));
   uint2 e = move_entry(trans, v - 12u * wq, pc8);
   if (v < 65532u && wq != thrT[__dp4a((int)e.y, (int)env, (int)e.x)]) return;  // not rare
-  const int t = k + 4 * q;
   const uint32_t slow0 = (uint32_t)((uint64_t)j * g.Cx + (uint32_t)(w << 4));
   const U4 sl = philox(slow0 + (uint32_t)t, (uint32_t)P, (uint32_t)(P >> 32), TAG_SLOW, g.k0, g.k1);
   if (v >= 65532u) {
@@ -404,33 +329,45 @@ __device__ __forceinline__ void exact_pair(const Geo &g, const PhaseU &u, const 
                       (v < 65532u ? ((uint64_t)wq << 32) + sl.x < 5461ull * thr : sl.x < thr);
   if (accept) {
     const uint32_t x = move_nibble(e.y);
-    apply_moves<kMode, false>(g, u, jr, w, 16, (x >> 2) << (2 * t), (x & 3u) << (2 * t));
+    apply_moves<kMode, false>(g, u, jr, w, n, (x >> 2) << (2 * t), (x & 3u) << (2 * t));
   }
 }
 
-// One word of a staged tile (all 32 lanes of the warp take part, one word
-// each): the fast decisions are applied; then, for every lane with rare calls
-// (about one word in 250), the warp decides that word's rare pairs together,
-// one pair a lane (16 lanes for the two calls), from the owner's inputs.  The
-// rare pairs were rejected by the fast path, and no other pair of the phase
-// touches their sites or neighbours, so the order does not matter.
-template <class Keys>
-__device__ __forceinline__ void tile_word(const Geo &g, const PhaseU &u, const uint2 *trans,
+// One word's pairs by one lane, with all 32 lanes of the warp calling
+// together (inactive lanes: active false): the fast decisions are applied;
+// then, for every lane with rare calls (about one word in 250), the warp
+// decides that word's rare pairs together, one pair a lane, from the owner's
+// inputs.  The rare pairs were rejected by the fast path, and no other pair of
+// the phase touches their sites or neighbours, so the order does not matter.
+// j: the a word's row in the class (keys the random streams); jr: its row in
+// u's arrays (j itself for a lattice in global memory, the row inside a
+// staged tile otherwise); near128: 128 if the phase's partners are nearest
+// neighbours, else 0; keys: the source of the Philox keys (SeedKeys or
+// TableKeys of the lattice's seed); kTPW threads share the word, this lane is
+// thread `sub` of them (see fast_moves).
+template <int kMode, int kTPW = 1, class Keys = SeedKeys>
+__device__ __forceinline__ void warp_word(const Geo &g, const PhaseU &u, const uint2 *trans,
                                           const uint16_t *thrT, const uint32_t *thr32, int j,
                                           int jr, int w, uint64_t P, uint32_t near128,
-                                          const Keys &keys) {
-  const WordIn in = gather<kRowTile>(g, u, jr, w, 16);
-  const uint3 d = fast_moves<1>(g, trans, thrT, j, w, 0, in, P, near128, keys);
-  apply_moves<kRowTile, true>(g, u, jr, w, 16, d.x, d.y);
-  unsigned ball = __ballot_sync(0xFFFFFFFFu, d.z != 0u);
+                                          const Keys &keys, int sub = 0, bool active = true) {
+  const int n = active ? (kMode == kRowGeneral ? min(16, g.Cx - (w << 4)) : 16) : 0;
+  WordIn in{};
+  uint32_t rz = 0u;
+  if (active) {
+    in = gather<kMode>(g, u, jr, w, n);
+    const uint3 d = fast_moves<kTPW>(g, trans, thrT, j, w, sub, in, P, near128, keys);
+    apply_moves<kMode, kTPW == 1>(g, u, jr, w, n, d.x, d.y);
+    rz = d.z;
+  }
+  unsigned ball = __ballot_sync(0xFFFFFFFFu, rz != 0u);
   if (ball) {
     const int lane = threadIdx.x & 31;
-    __syncwarp();  // the fast moves of every lane are in shared memory
+    __syncwarp();  // the fast moves of every lane are in memory
 #pragma unroll 1
     while (ball) {
       const int src = __ffs(ball) - 1;
       ball &= ball - 1u;
-      const uint32_t rz = __shfl_sync(0xFFFFFFFFu, d.z, src);
+      const uint32_t orz = __shfl_sync(0xFFFFFFFFu, rz, src);
       WordIn o;
       o.A = __shfl_sync(0xFFFFFFFFu, in.A, src);
       o.B = __shfl_sync(0xFFFFFFFFu, in.B, src);
@@ -443,11 +380,20 @@ __device__ __forceinline__ void tile_word(const Geo &g, const PhaseU &u, const u
       o.sb.ge = __shfl_sync(0xFFFFFFFFu, in.sb.ge, src);
       o.sb.go = __shfl_sync(0xFFFFFFFFu, in.sb.go, src);
       const int oj = __shfl_sync(0xFFFFFFFFu, j, src), ojr = __shfl_sync(0xFFFFFFFFu, jr, src),
-                ow = __shfl_sync(0xFFFFFFFFu, w, src);
-      const int c = (lane >> 3) & 1;
-      if (lane < 16 && ((rz >> c) & 1u))
-        exact_pair<kRowTile>(g, u, trans, thrT, thr32, oj, ojr, ow, c, (lane >> 2) & 1, lane & 3,
-                             o, P, near128);
+                ow = __shfl_sync(0xFFFFFFFFu, w, src), on = __shfl_sync(0xFFFFFFFFu, n, src);
+      // the owner's pairs, one a lane: 16 (both calls), 8 (one call) or 4
+      int c, h;
+      if constexpr (kTPW == 1) {
+        c = (lane >> 3) & 1;
+        h = (lane >> 2) & 1;
+      } else {
+        const int osub = __shfl_sync(0xFFFFFFFFu, sub, src);
+        c = kTPW == 2 ? osub : osub >> 1;
+        h = kTPW == 2 ? (lane >> 2) & 1 : osub & 1;
+      }
+      if (lane < 16 / kTPW && ((orz >> c) & 1u))
+        exact_pair<kMode>(g, u, trans, thrT, thr32, oj, ojr, ow, on, c, h, lane & 3, o, P,
+                          near128);
     }
   }
 }
@@ -480,19 +426,15 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint16_t *th
   const PhaseU u = phase_uniform(g, sc);
   const uint32_t near128 = sc.near ? 128u : 0u;
   const int nw = g.Cy * g.W;
-  int wid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
-  int j = wid / g.W, w = wid - j * g.W;
-  const int sj = stride / g.W, sw = stride - sj * g.W;
-  for (; wid < nw; wid += stride) {
-    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrT, thr32, j, j, w, P,
-                                                      near128, SeedKeys{g.k0, g.k1});
-    w += sw;
-    j += sj;
-    if (w >= g.W) {
-      w -= g.W;
-      ++j;
-    }
+  // a trip count uniform across the block, so that every warp's lanes stay
+  // together for the cooperative exact path
+  for (int base = blockIdx.x * blockDim.x; base < nw; base += stride) {
+    const int wid = base + threadIdx.x;
+    const bool act = wid < nw;
+    const int j = act ? wid / g.W : 0, w = act ? wid - j * g.W : 0;
+    warp_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrT, thr32, j, j, w, P,
+                                                     near128, SeedKeys{g.k0, g.k1}, 0, act);
   }
 }
 
@@ -777,7 +719,8 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint16_t *thrT,
     }
     const int tile = sm.tile[b];
     if (tile < 0) break;
-    tile_word(g, local_u(b), sm.trans, sm.thrT, thr32, tile * R + jr, jr, w, P, near128, keys);
+    warp_word<kRowTile>(g, local_u(b), sm.trans, sm.thrT, thr32, tile * R + jr, jr, w, P, near128,
+                        keys);
     // (2) this warp is done with the tile: its shared-memory writes are ordered
     // before the async copies that will refill the buffer, and before the
     // last warp's reads
@@ -901,19 +844,13 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
   const PhaseU u = phase_uniform(g, sc);
   const uint32_t near128 = sc.near ? 128u : 0u;
   const int nw = g.Cy * g.W;
-  int wid = ((int)blockIdx.x - J.cta_begin) * blockDim.x + threadIdx.x;
   const int stride = J.cta_count * blockDim.x;
-  int j = wid / g.W, w = wid - j * g.W;
-  const int sj = stride / g.W, sw = stride - sj * g.W;
-  for (; wid < nw; wid += stride) {
-    phase_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrT, J.thr32, j, j, w,
-                                                      P, near128, SeedKeys{g.k0, g.k1});
-    w += sw;
-    j += sj;
-    if (w >= g.W) {
-      w -= g.W;
-      ++j;
-    }
+  for (int base = ((int)blockIdx.x - J.cta_begin) * blockDim.x; base < nw; base += stride) {
+    const int wid = base + threadIdx.x;
+    const bool act = wid < nw;
+    const int j = act ? wid / g.W : 0, w = act ? wid - j * g.W : 0;
+    warp_word<kAligned ? kRowAligned : kRowGeneral>(g, u, sm.trans, sm.thrT, J.thr32, j, j, w, P,
+                                                     near128, SeedKeys{g.k0, g.k1}, 0, act);
   }
 }
 
@@ -925,7 +862,7 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
 // when due; then it writes the lattice back and takes the next one.  The same
 // per-word code as phase_kernel runs against shared memory, so results are
 // identical to the per-phase launches.
-__global__ void __launch_bounds__(256, 2) resident_kernel(const JobDesc *__restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(512, 1) resident_kernel(const JobDesc *__restrict__ jobs, int njobs,
                                                        int *queue) {
   extern __shared__ __align__(16) uint32_t dyn[];
   uint16_t *s_thrT = reinterpret_cast<uint16_t *>(dyn);
@@ -956,11 +893,10 @@ __global__ void __launch_bounds__(256, 2) resident_kernel(const JobDesc *__restr
     gs.words = s_words;
     const bool aligned = (g.Cx & 15) == 0;
     const int nwa = g.Cy * g.W;  // a-words per phase
-    // threads a word: as given, else the most (four, two) that still take a
-    // phase's words in one pass of the CTA, else one
-    const int tpw = J.tpw > 0 ? J.tpw
-                  : 4 * nwa <= (int)blockDim.x ? 4
-                  : 2 * nwa <= (int)blockDim.x ? 2 : 1;
+    // threads a word: the most (four, two; at most J.max_tpw) that still take
+    // a phase's words in one pass of the CTA, else one
+    const int tpw = J.max_tpw >= 4 && 4 * nwa <= (int)blockDim.x ? 4
+                  : J.max_tpw >= 2 && 2 * nwa <= (int)blockDim.x ? 2 : 1;
     // thread 0's copies of the record count and its ring slot: read once per
     // job, so that a record costs no global load on the sweep's critical path
     int64_t obs_cnt = 0, obs_slot = 0;
@@ -987,28 +923,33 @@ __global__ void __launch_bounds__(256, 2) resident_kernel(const JobDesc *__restr
         const uint64_t P = (uint64_t)(P0 + 8 * s + p);
         const PhaseU &u = s_u[p];  // read from shared memory where used
         const uint32_t near128 = s_sched[p].near ? 128u : 0u;
-        for (int i = threadIdx.x; i < tpw * nwa; i += blockDim.x) {
-          const int wid = tpw == 1 ? i : (tpw == 2 ? i >> 1 : i >> 2), sub = i - tpw * wid;
+        for (int base = 0; base < tpw * nwa; base += blockDim.x) {  // uniform trip count
+          const int i = base + threadIdx.x;
+          const bool act = i < tpw * nwa;
+          const int wid = !act ? 0 : tpw == 1 ? i : (tpw == 2 ? i >> 1 : i >> 2);
+          const int sub = act ? i - tpw * wid : 0;
           const int j = wid / g.W, w = wid - j * g.W;
           const SeedKeys keys{gs.k0, gs.k1};
           if (aligned) {
             if (tpw == 1)
-              phase_word<kRowAligned, 1>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys);
+              warp_word<kRowAligned, 1>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
+                                        sub, act);
             else if (tpw == 2)
-              phase_word<kRowAligned, 2>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
-                                         sub);
+              warp_word<kRowAligned, 2>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
+                                        sub, act);
             else
-              phase_word<kRowAligned, 4>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
-                                         sub);
+              warp_word<kRowAligned, 4>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
+                                        sub, act);
           } else {
             if (tpw == 1)
-              phase_word<kRowGeneral, 1>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys);
+              warp_word<kRowGeneral, 1>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
+                                        sub, act);
             else if (tpw == 2)
-              phase_word<kRowGeneral, 2>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
-                                         sub);
+              warp_word<kRowGeneral, 2>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
+                                        sub, act);
             else
-              phase_word<kRowGeneral, 4>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
-                                         sub);
+              warp_word<kRowGeneral, 4>(gs, u, s_trans, s_thrT, J.thr32, j, j, w, P, near128, keys,
+                                        sub, act);
           }
         }
         __syncthreads();

@@ -77,8 +77,10 @@ def test_batch_equals_individual_sweeps_and_oracle(cc):
         assert np.array_equal(got[i][0], st) and np.array_equal(got[i][1], rec), MIX[i]
 
 
-@pytest.mark.parametrize("cfg", [(64, 1 << 17, 1), (128, 1 << 17, 4), (256, 1 << 17, 8),
-                                 (256, 4096, 2)])
+@pytest.mark.parametrize("cfg", [(64, 1 << 17, 1, 4), (128, 1 << 17, 4, 4), (256, 1 << 17, 8, 4),
+                                 (256, 4096, 2, 4), (256, 1 << 17, 2, 1), (256, 1 << 17, 2, 2),
+                                 (512, 1 << 17, 1, 1), (512, 1 << 17, 1, 2),
+                                 (512, 1 << 17, 1, 4), (128, 1 << 17, 2, 2)])
 def test_batch_results_do_not_depend_on_launch_shape(cc, cfg):
     """Launch shapes the autotuner may pick, including a resident limit that
     sends the larger lattices down the per-phase path."""
@@ -135,6 +137,8 @@ def test_batch_rejects_bad_use(cc):
             b.sweep(2, 1.0, 0.0, 1.0, 1.0)
         with pytest.raises(cc.CcmcError):
             b.config(100, 1 << 16, 2)
+        with pytest.raises(cc.CcmcError):
+            b.config(256, 1 << 16, 2, 3)  # threads a word: 1, 2 or 4
     a.close()
     b_.close()
 
