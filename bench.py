@@ -480,10 +480,13 @@ def measure_paper_maps(cc, L=4096, nmaps=40, batch=8):
     }
 
 
-def measure_served(cc, count=120, plain_sample=24):
+def measure_served(cc, count=2000, plain_every=125):
     """Poisson request stream (200 req/s; L log-uniform in [32, 2048]; sweeps
     log-uniform in [1e3, 1e5]) through the continuous-batching server under a
-    120 GB budget; p50/p99 latency from submission to completion."""
+    120 GB budget; p50/p99 latency from submission to completion.  Beside it,
+    a stated subset of the same requests (every plain_every-th) runs one at a
+    time, uncapped, through the plain single-lattice path; their final
+    observables must equal the served ones."""
     import numpy as np
 
     from workloads import request_stream
@@ -500,29 +503,36 @@ def measure_served(cc, count=120, plain_sample=24):
     res = [srv.wait(t, timeout_s=3600.0) for t in tickets]
     stats = srv.stats()
     srv.stop()
-    lat = np.array([r["done_s"] - r["submit_s"] for r in res])
-    work = sum(r["site_updates"] for r in res)
-    span = max(r["done_s"] for r in res) - min(r["submit_s"] for r in res)
+    ok = [r for r in res if r["status"] == 0]
+    lat = np.array([r["done_s"] - r["submit_s"] for r in ok])
+    work = sum(r["site_updates"] for r in ok)
+    span = max(r["done_s"] for r in ok) - min(r["submit_s"] for r in res)
     offered = sum(s.sites * s.nsweeps for s in sims) / max(arrivals[-1], 1e-9)
-    sub = sims[:plain_sample]
-    cap = 2000  # a lone small lattice is launch-bound: bound the sample's run time
-    tp = time.perf_counter()
-    for s in sub:
+    picked = list(range(0, count, plain_every))
+    t_plain, identical = 0.0, True
+    keys = ("Nc", "BV", "BJ", "M", "M_stag", "S_sum", "S_stag", "sweeps_done")
+    for i in picked:
+        s = sims[i]
+        tp = time.perf_counter()
         with cc.Lattice(s.Lx, s.Ly) as one:
             one.init_constrained(s.seed, s.n, s.charged_frac)
-            one.sweep(min(s.nsweeps, cap), s.beta, s.Delta, s.V, s.J)
-            one.observables()
-    plain = sum(s.sites * min(s.nsweeps, cap) for s in sub) / (time.perf_counter() - tp)
+            one.sweep(s.nsweeps, s.beta, s.Delta, s.V, s.J)
+            obs = one.observables()
+        t_plain += time.perf_counter() - tp
+        identical &= all(obs[k] == res[i]["final_obs"][k] for k in keys)
+    plain = sum(sims[i].sites * sims[i].nsweeps for i in picked) / t_plain
     return {"workload": f"{count} Poisson requests at 200/s (L log-U[32,2048], sweeps "
                         "log-U[1e3,1e5], T~U[0.1,3], n~U[0,.4], Delta~U[-1,1], V~U[0,2], J=1), "
-                        "120 GB budget",
+                        "120 GB budget, at most 1024 running, 20 ms slices",
             "value": work / span, "unit": "site-updates/s", "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "offered": offered,
-            "completed": stats["completed"], "slices": stats["slices"],
+            "completed": stats["completed"], "failed": stats["failed"],
+            "rejected": stats["rejected"], "slices": stats["slices"], "span_s": span,
             "plain_back_to_back": {"value": plain, "unit": "site-updates/s",
-                                   "sample": f"first {plain_sample} requests one at a time "
-                                             f"(init, ccmc_sweep, observables), at most {cap} "
-                                             "sweeps each"},
+                                   "sample": f"{len(picked)} of the requests (every "
+                                             f"{plain_every}th), uncapped, one at a time "
+                                             "(init, ccmc_sweep, observables)",
+                                   "identical_final_observables": identical},
             "speedup_vs_plain": (work / span) / plain}
 
 
@@ -717,17 +727,44 @@ def run_ours(args):
         line["roofline"]["phase_share"] = (8 * step_sweeps * len(sims) * m["phase_ms"]
                                            / (1e3 * m["total_s"] / args.steps))
         if not args.no_side:
+            peaks = measure_peaks(cc)
+            line["peaks"] = peaks
             if args.workload == "large16384":
-                line["temperature4096"] = measure_temperature(cc, args, peak, peak_kind, local)
-            line["batched"] = measure_batched(cc)
+                t = measure_temperature(cc, args, peak, peak_kind, local)
+                t["l2_roofline"] = onchip_roofline("l2", 1.5 * t["value"] / 1e9, peaks)
+                line["temperature4096"] = t
+            b = measure_batched(cc)
+            b["roofline"] = onchip_roofline("smem", 1.5 * b["value"] / 1e9, peaks)
+            line["batched"] = b
             line["served"] = measure_served(cc, count=args.served_requests)
             line["paper_maps"] = measure_paper_maps(cc)
-            line["small16"] = measure_small(cc)
+            sm = measure_small(cc)
+            sm["roofline"] = onchip_roofline("smem", 1.5 * 256 / (sm["batched_us_per_sweep"] * 1e-6)
+                                             / 1e9, peaks)
+            line["small16"] = sm
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample(sims)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def measure_peaks(cc):
+    """The device's measured on-chip read bandwidths (the shared-memory and L2
+    paths' roofline denominators): every SM streaming conflict-free 16-byte
+    shared-memory reads, and 16-byte L1-bypassing reads of a 64 MB buffer that
+    L2 holds."""
+    return {"smem_gbs": cc.peak_smem_read() / 1e9, "l2_gbs": cc.peak_l2_read(64 << 20) / 1e9,
+            "how": "ccmc_peak_smem_read / ccmc_peak_l2_read(64 MB): one timed launch after a "
+                   "warm-up, CUDA events"}
+
+
+def onchip_roofline(bound, achieved_gbs, peaks):
+    """Roofline object of a path bound by on-chip memory: 1.5 algorithmic bytes
+    a site-update over the measured shared-memory (smem) or L2 read peak."""
+    p = peaks["smem_gbs" if bound == "smem" else "l2_gbs"]
+    return {"bound": bound, "achieved": achieved_gbs, "peak": p, "unit": "GB/s",
+            "frac": achieved_gbs / p, "traffic": None, "peak_source": "measured on this device"}
 
 
 def measure_temperature(cc, args, peak, peak_kind, local):

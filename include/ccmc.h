@@ -283,6 +283,19 @@ int ccmc_selftest_wait(uint32_t polls);
 int ccmc_philox_device(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                        uint32_t k1, int64_t count, uint32_t *out);
 
+/* Diagnostics (the paper has no counterpart): measured read bandwidth of the
+ * current device's on-chip memories, the peaks against which the shared-memory
+ * and L2 paths' rooflines are stated.  ccmc_peak_smem_read: every SM's
+ * resident CTAs stream conflict-free 16-byte reads of their own shared-memory
+ * buffer (32 KB each); ccmc_peak_l2_read: all SMs stream 16-byte reads that
+ * bypass L1 over a device buffer of buffer_bytes (1 MiB .. 1 GiB; pick one
+ * that L2 holds), after a pass that brings it into L2.  Each times one launch
+ * with CUDA events after a warm-up launch, synchronously on the legacy default
+ * stream, and writes bytes per second.  Errors: E_INVAL (null pointer, size
+ * out of range), E_NOMEM, E_CUDA. */
+int ccmc_peak_smem_read(double *bytes_per_s);
+int ccmc_peak_l2_read(int64_t buffer_bytes, double *bytes_per_s);
+
 /* ---- Paper-faithful map mode (Sec. 3.2, the algorithm for building a map) --
  * The paper's own parallel scheme: maps of non-interacting pairs built on the
  * host by random marking, copied to the GPU and processed one after another,

@@ -90,6 +90,8 @@ def _load():
         "ccmc_sync": (c_int, [vp]),
         "ccmc_philox_device": (c_int, [c_uint32] * 6 + [c_int64, u32p]),
         "ccmc_selftest_wait": (c_int, [c_uint32]),
+        "ccmc_peak_smem_read": (c_int, [POINTER(c_double)]),
+        "ccmc_peak_l2_read": (c_int, [c_int64, POINTER(c_double)]),
         "ccmc_batch_create": (c_int, [c_int, POINTER(vp), vp, POINTER(vp)]),
         "ccmc_batch_destroy": (c_int, [vp]),
         "ccmc_batch_config": (c_int, [vp, c_int, c_int64, c_int, c_int]),
@@ -162,6 +164,20 @@ def selftest_wait(polls: int = 1 << 16) -> int:
     """The bounded-wait self-test: a device wait on a barrier nothing completes
     gives up after `polls` polls; returns the call's code (E_TIMEOUT expected)."""
     return lib().ccmc_selftest_wait(polls)
+
+
+def peak_smem_read() -> float:
+    """Measured shared-memory read bandwidth of the current device (bytes/s)."""
+    x = c_double()
+    _check(lib().ccmc_peak_smem_read(ctypes.byref(x)), "ccmc_peak_smem_read")
+    return x.value
+
+
+def peak_l2_read(buffer_bytes: int = 64 << 20) -> float:
+    """Measured L2 read bandwidth over an L2-resident buffer (bytes/s)."""
+    x = c_double()
+    _check(lib().ccmc_peak_l2_read(buffer_bytes, ctypes.byref(x)), "ccmc_peak_l2_read")
+    return x.value
 
 
 def map_size(Lx: int, Ly: int) -> int:

@@ -1,6 +1,6 @@
 """Build ``libccmc.so`` in-tree (``paper_2301_11735_gb300/_build``) for sm_103a.
 
-Eight translation units are compiled in parallel and linked into one shared
+Nine translation units are compiled in parallel and linked into one shared
 library that exports the C ABI of ``include/ccmc.h``:
 
 * ``csrc/ccmc_phase.cu``   -- the colour-phase kernels (nvcc, sm_103a only);
@@ -9,6 +9,7 @@ library that exports the C ABI of ``include/ccmc.h``:
 * ``csrc/ccmc_kernels.cu`` -- the other CUDA kernels (init, recount, packing);
 * ``csrc/ccmc_api.cu``     -- host code of the C ABI (nvcc host pass);
 * ``csrc/ccmc_noalloc.cu`` -- the recount entry point that allocates nothing;
+* ``csrc/ccmc_peaks.cu``   -- measured shared-memory and L2 read bandwidth (diagnostics);
 * ``csrc/ccmc_tables.cpp`` -- FP64 threshold tables (g++);
 * ``csrc/ccmc_server.cpp`` -- the continuous-batching server (g++, a host thread).
 
@@ -69,6 +70,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         "ccmc_kernels.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_kernels.cu")],
         "ccmc_api.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_api.cu")],
         "ccmc_noalloc.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_noalloc.cu")],
+        "ccmc_peaks.o": [nvcc, "-c", *common, os.path.join(CSRC, "ccmc_peaks.cu")],
         "ccmc_tables.o": [os.environ.get("CXX", "g++"), "-c", "-std=c++17", "-O2", "-fPIC",
                           "-ffp-contract=off", f"-I{cuda}/include",
                           os.path.join(CSRC, "ccmc_tables.cpp")],

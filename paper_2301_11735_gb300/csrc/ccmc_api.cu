@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -44,6 +45,50 @@ constexpr int kChunk = 16;
 // tails.
 constexpr int kLockstepMin = 8;
 constexpr int64_t kLockstepMaxWords = 16384;
+
+// Lattice memory comes from a library-owned stream-ordered pool per device
+// (allocations and frees queued on the lattice's stream, memory kept cached
+// in the pool): creating and destroying lattices then never synchronises the
+// device, which a server admitting and retiring simulations while others run
+// depends on.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaMemPool_t lattice_pool(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = p;
+  }
+  return g_pool[dev];
+}
+
+// bytes of device memory for a lattice of device dev, ordered on stream s
+bool dalloc(void **p, size_t bytes, int dev, cudaStream_t s) {
+  cudaMemPool_t pool = lattice_pool(dev);
+  if (!pool || cudaMallocFromPoolAsync(p, bytes, pool, s) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  return true;
+}
+
+void dfree(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
 
 }  // namespace
 
@@ -223,32 +268,8 @@ int check_status(ccmc_lattice *h) {
 
 }  // namespace
 
-extern "C" {
-
-const char *ccmc_strerror(int code) {
-  switch (code) {
-    case CCMC_OK: return "ok";
-    case CCMC_E_INVAL: return "invalid argument";
-    case CCMC_E_NOMEM: return "out of memory";
-    case CCMC_E_CUDA: return "CUDA error";
-    case CCMC_E_TIMEOUT: return "device wait timed out";
-    case CCMC_E_BUDGET: return "memory budget exhausted";
-    case CCMC_E_STATE: return "call out of order";
-    case CCMC_E_NOTFOUND: return "not found";
-    default: return "unknown error";
-  }
-}
-
-int ccmc_threshold_table(double beta, double Delta, double V, double J, uint32_t *out) {
-  if (!out || !(beta >= 0.0) || !std::isfinite(Delta) || !std::isfinite(V) ||
-      !std::isfinite(J))
-    return CCMC_E_INVAL;
-  build_thresholds(beta, Delta, V, J, out);
-  return CCMC_OK;
-}
-
-int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
-                        ccmc_lattice **out) {
+int ccmc::lattice_new(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity, bool wait,
+                      ccmc_lattice **out) {
   if (!out) return CCMC_E_INVAL;
   *out = nullptr;
   int rc = validate_shape(Lx, Ly);
@@ -294,14 +315,15 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
     h->own_stream = true;
   }
   const int np = recount_grid(g);
-  if (cudaMalloc(&h->d_words, sizeof(uint32_t) * 16 * g.cstride) != cudaSuccess ||
-      cudaMalloc(&h->d_ctl, sizeof(int64_t) * kCtlWords) != cudaSuccess ||
-      cudaMalloc(&h->d_partials, sizeof(int64_t) * 7 * np) != cudaSuccess ||
-      cudaMalloc(&h->d_ring, sizeof(int64_t) * 8 * h->ring_cap) != cudaSuccess ||
-      cudaMalloc(&h->d_flag, sizeof(int)) != cudaSuccess)
-    return fail(CCMC_E_NOMEM);
+  const int dev = h->device;
   const size_t tb = sizeof(uint32_t) * (kTableN + 2 * kMoveN) + sizeof(uint16_t) * kThrT;
-  if (cudaMalloc(&h->d_tables, tb) != cudaSuccess) return fail(CCMC_E_NOMEM);
+  if (!dalloc((void **)&h->d_words, sizeof(uint32_t) * 16 * g.cstride, dev, h->stream) ||
+      !dalloc((void **)&h->d_ctl, sizeof(int64_t) * kCtlWords, dev, h->stream) ||
+      !dalloc((void **)&h->d_partials, sizeof(int64_t) * 7 * np, dev, h->stream) ||
+      !dalloc((void **)&h->d_ring, sizeof(int64_t) * 8 * h->ring_cap, dev, h->stream) ||
+      !dalloc((void **)&h->d_flag, sizeof(int), dev, h->stream) ||
+      !dalloc(&h->d_tables, tb, dev, h->stream))
+    return fail(CCMC_E_NOMEM);
   // the threshold levels and the move table one after another (a multiple of
   // 16 bytes from a 256-byte aligned base): the tile kernels copy them into
   // shared memory with one bulk copy; thr32 after them
@@ -320,32 +342,20 @@ int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
       cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t) * 16 * g.cstride, h->stream) !=
           cudaSuccess ||
       launch_set_ctl(h->d_ctl, 0, h->stream) != cudaSuccess ||
-      cudaStreamSynchronize(h->stream) != cudaSuccess)
+      (wait && cudaStreamSynchronize(h->stream) != cudaSuccess))
     return fail(CCMC_E_CUDA);
   *out = h;
   return CCMC_OK;
 }
 
-int ccmc_lattice_destroy(ccmc_lattice *h) {
-  if (!h) return CCMC_E_INVAL;
-  if (h->stream) cudaStreamSynchronize(h->stream);
-  drop_graphs(h);
-  cudaFree(h->d_words);
-  cudaFree(h->d_ctl);
-  cudaFree(h->d_partials);
-  cudaFree(h->d_ring);
-  cudaFree(h->d_hist);
-  cudaFree(h->d_tables);
-  cudaFree(h->d_bytes);
-  cudaFree(h->d_flag);
-  cudaFree(h->d_maps);
-  if (h->map_ev) cudaEventDestroy(h->map_ev);
-  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
-  delete h;
+static int ensure_bytes(ccmc_lattice *h) {
+  if (h->d_bytes) return CCMC_OK;
+  const size_t N = (size_t)h->g.Lx * h->g.Ly;
+  if (!dalloc((void **)&h->d_bytes, N, h->device, h->stream)) return CCMC_E_NOMEM;
   return CCMC_OK;
 }
 
-int ccmc_init_counts(ccmc_lattice *h, uint64_t seed, int64_t n_plus, int64_t n_minus) {
+int ccmc::init_counts_async(ccmc_lattice *h, uint64_t seed, int64_t n_plus, int64_t n_minus) {
   if (!h) return CCMC_E_INVAL;
   const int64_t N = (int64_t)h->g.Lx * h->g.Ly;
   if (n_plus < 0 || n_minus < 0 || n_plus + n_minus > N) return CCMC_E_INVAL;
@@ -355,11 +365,10 @@ int ccmc_init_counts(ccmc_lattice *h, uint64_t seed, int64_t n_plus, int64_t n_m
   if (h->d_hist) CK(cudaMemsetAsync(h->d_hist, 0, sizeof(int64_t) * 3 * h->nbins, h->stream));
   h->phases_done = 0;
   h->initialised = true;
-  CK(cudaStreamSynchronize(h->stream));
   return CCMC_OK;
 }
 
-int ccmc_init_constrained(ccmc_lattice *h, uint64_t seed, double n, double charged_frac) {
+int ccmc::init_constrained_async(ccmc_lattice *h, uint64_t seed, double n, double charged_frac) {
   if (!h) return CCMC_E_INVAL;
   if (!std::isfinite(n)) return CCMC_E_INVAL;
   if (charged_frac < 0.0) charged_frac = 0.3;
@@ -371,7 +380,116 @@ int ccmc_init_constrained(ccmc_lattice *h, uint64_t seed, double n, double charg
   if (C < aQ) C = aQ;
   if ((C - Q) & 1) C += 1;
   if (C > N) return CCMC_E_INVAL;
-  return ccmc_init_counts(h, seed, (C + Q) / 2, (C - Q) / 2);
+  return init_counts_async(h, seed, (C + Q) / 2, (C - Q) / 2);
+}
+
+int ccmc::export_async(ccmc_lattice *h, int64_t *rec, int64_t *status, int64_t *count,
+                       int64_t *ring, uint8_t *state, cudaEvent_t ready) {
+  if (!h || !rec || !status || !h->initialised) return CCMC_E_INVAL;
+  int rc = write_recount_latest(h);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(rec, h->d_ctl + kCtlLatest, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(status, h->d_ctl + kCtlStatus, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                     h->stream));
+  if (ring) {
+    if (!count) return CCMC_E_INVAL;
+    CK(cudaMemcpyAsync(count, h->d_ctl + kCtlObsCount, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaMemcpyAsync(ring, h->d_ring, sizeof(int64_t) * 8 * h->ring_cap,
+                       cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (state) {
+    rc = ensure_bytes(h);
+    if (rc) return rc;
+    CK(launch_unpack(h->g, h->d_bytes, h->stream));
+    CK(cudaMemcpyAsync(state, h->d_bytes, (size_t)h->g.Lx * h->g.Ly, cudaMemcpyDeviceToHost,
+                       h->stream));
+  }
+  CK(cudaEventRecord(ready, h->stream));
+  return CCMC_OK;
+}
+
+void ccmc::obs_of_record(const ccmc_lattice *h, const int64_t *rec, ccmc_obs *out) {
+  int64_t r[8];
+  std::memcpy(r, rec, sizeof(r));
+  r[0] = h->phases_done / 8;
+  fill_obs(h, r, out);
+}
+
+int64_t ccmc::series_of_ring(const ccmc_lattice *h, const int64_t *ring, int64_t count,
+                             ccmc_obs *out, int64_t cap) {
+  const int64_t held = count < h->ring_cap ? count : h->ring_cap;
+  int64_t n = 0;
+  for (int64_t r = count - held; r < count && n < cap; ++r, ++n)
+    fill_obs(h, ring + 8 * (r % h->ring_cap), out + n);
+  return n;
+}
+
+int64_t ccmc::ring_capacity(const ccmc_lattice *h) { return h->ring_cap; }
+
+cudaStream_t ccmc::lattice_stream(const ccmc_lattice *h) { return h->stream; }
+
+extern "C" {
+
+const char *ccmc_strerror(int code) {
+  switch (code) {
+    case CCMC_OK: return "ok";
+    case CCMC_E_INVAL: return "invalid argument";
+    case CCMC_E_NOMEM: return "out of memory";
+    case CCMC_E_CUDA: return "CUDA error";
+    case CCMC_E_TIMEOUT: return "device wait timed out";
+    case CCMC_E_BUDGET: return "memory budget exhausted";
+    case CCMC_E_STATE: return "call out of order";
+    case CCMC_E_NOTFOUND: return "not found";
+    default: return "unknown error";
+  }
+}
+
+int ccmc_threshold_table(double beta, double Delta, double V, double J, uint32_t *out) {
+  if (!out || !(beta >= 0.0) || !std::isfinite(Delta) || !std::isfinite(V) ||
+      !std::isfinite(J))
+    return CCMC_E_INVAL;
+  build_thresholds(beta, Delta, V, J, out);
+  return CCMC_OK;
+}
+
+int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
+                        ccmc_lattice **out) {
+  return lattice_new(Lx, Ly, cuda_stream, obs_capacity, true, out);
+}
+
+int ccmc_lattice_destroy(ccmc_lattice *h) {
+  if (!h) return CCMC_E_INVAL;
+  if (h->stream) cudaStreamSynchronize(h->stream);  // this lattice's work only
+  drop_graphs(h);
+  dfree(h->d_words, h->stream);
+  dfree(h->d_ctl, h->stream);
+  dfree(h->d_partials, h->stream);
+  dfree(h->d_ring, h->stream);
+  dfree(h->d_hist, h->stream);
+  dfree(h->d_tables, h->stream);
+  dfree(h->d_bytes, h->stream);
+  dfree(h->d_flag, h->stream);
+  dfree(h->d_maps, h->stream);
+  if (h->map_ev) cudaEventDestroy(h->map_ev);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return CCMC_OK;
+}
+
+int ccmc_init_counts(ccmc_lattice *h, uint64_t seed, int64_t n_plus, int64_t n_minus) {
+  const int rc = init_counts_async(h, seed, n_plus, n_minus);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return CCMC_OK;
+}
+
+int ccmc_init_constrained(ccmc_lattice *h, uint64_t seed, double n, double charged_frac) {
+  const int rc = init_constrained_async(h, seed, n, charged_frac);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return CCMC_OK;
 }
 
 int ccmc_sweep(ccmc_lattice *h, int64_t nsweeps, double beta, double Delta, double V, double J,
@@ -448,14 +566,11 @@ int ccmc_map_apply(ccmc_lattice *h, const int32_t *pairs, int64_t map0, int64_t 
   if (!h->map_ev && cudaEventCreateWithFlags(&h->map_ev, cudaEventDisableTiming) != cudaSuccess)
     return CCMC_E_CUDA;
   if (n > h->map_cap) {
-    CK(cudaStreamSynchronize(h->stream));  // earlier maps may still be in use
-    cudaFree(h->d_maps);
+    dfree(h->d_maps, h->stream);  // after the earlier maps' work on the stream
     h->d_maps = nullptr;
     h->map_cap = 0;
-    if (cudaMalloc(&h->d_maps, sizeof(int32_t) * n) != cudaSuccess) {
-      cudaGetLastError();
+    if (!dalloc((void **)&h->d_maps, sizeof(int32_t) * n, h->device, h->stream))
       return CCMC_E_NOMEM;
-    }
     h->map_cap = n;
   }
   int rc = upload_params(h, beta, Delta, V, J);
@@ -506,10 +621,11 @@ int ccmc_hist_enable(ccmc_lattice *h, int nbins) {
   if (!h || nbins < 1 || nbins > (1 << 20)) return CCMC_E_INVAL;
   CK(cudaStreamSynchronize(h->stream));
   drop_graphs(h);  // captured recounts hold the old histogram pointer
-  cudaFree(h->d_hist);
+  dfree(h->d_hist, h->stream);
   h->d_hist = nullptr;
   h->nbins = 0;
-  if (cudaMalloc(&h->d_hist, sizeof(int64_t) * 3 * nbins) != cudaSuccess) return CCMC_E_NOMEM;
+  if (!dalloc((void **)&h->d_hist, sizeof(int64_t) * 3 * nbins, h->device, h->stream))
+    return CCMC_E_NOMEM;
   h->nbins = nbins;
   CK(cudaMemsetAsync(h->d_hist, 0, sizeof(int64_t) * 3 * nbins, h->stream));
   return CCMC_OK;
@@ -524,12 +640,6 @@ int ccmc_hist_get(ccmc_lattice *h, int64_t *out) {
   return CCMC_OK;
 }
 
-static int ensure_bytes(ccmc_lattice *h) {
-  if (h->d_bytes) return CCMC_OK;
-  const size_t N = (size_t)h->g.Lx * h->g.Ly;
-  if (cudaMalloc(&h->d_bytes, N) != cudaSuccess) return CCMC_E_NOMEM;
-  return CCMC_OK;
-}
 
 int ccmc_get_state(ccmc_lattice *h, uint8_t *host_out) {
   if (!h || !host_out) return CCMC_E_INVAL;

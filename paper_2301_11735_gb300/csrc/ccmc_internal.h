@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <vector>
 
+#include "../../include/ccmc.h"
+
 struct ccmc_lattice;
 struct ccmc_batch;
 
@@ -140,6 +142,31 @@ cudaError_t launch_resident(const JobDesc *d_jobs, int njobs, int *d_queue, int 
 int64_t resident_smem_bytes(int64_t max_words);
 cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                           uint32_t k1, int64_t count, uint32_t *out, cudaStream_t s);
+
+// ccmc_lattice_create without the final wait (wait false): the lattice's
+// memory, tables and zeroed state are queued on its stream.
+int lattice_new(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity, bool wait,
+                ccmc_lattice **out);
+
+// ccmc_init_counts / ccmc_init_constrained without the final wait.
+int init_counts_async(ccmc_lattice *h, uint64_t seed, int64_t n_plus, int64_t n_minus);
+int init_constrained_async(ccmc_lattice *h, uint64_t seed, double n, double charged_frac);
+
+// What a finished simulation reports, copied to pinned host memory by work
+// queued on its stream (then `ready` recorded there): rec (8 int64), the
+// latest exact recount (its word 0 is replaced by the sweeps done); status,
+// the device-side error flag; count and ring (8 int64 a record, ring_cap
+// records), the observable ring, when ring is not null; state (Lx Ly bytes),
+// the site codes, when state is not null.
+int export_async(ccmc_lattice *h, int64_t *rec, int64_t *status, int64_t *count, int64_t *ring,
+                 uint8_t *state, cudaEvent_t ready);
+// The observables of a record exported by export_async (its E from the
+// lattice's parameters), and the records of an exported ring, oldest first.
+void obs_of_record(const ccmc_lattice *h, const int64_t *rec, ccmc_obs *out);
+int64_t series_of_ring(const ccmc_lattice *h, const int64_t *ring, int64_t count, ccmc_obs *out,
+                       int64_t cap);
+int64_t ring_capacity(const ccmc_lattice *h);
+cudaStream_t lattice_stream(const ccmc_lattice *h);
 
 // A batch with no fixed members, room for `cap` lattices, on `stream`.
 int batch_new(int cap, cudaStream_t stream, ccmc_batch **out);
