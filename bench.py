@@ -62,17 +62,19 @@ OBS_EVERY = {"temperature4096": 10, "large16384": 1}
 # They hold only for the kernel sources they were taken with (kernel_digest);
 # after any change to those sources the bench reports them as null.
 PHASE_COUNTERS = {
-    "large16384": {"digest": "120d38af0d7a1b4eb54a9e80eb46a3e5110d63251cc6cdfd73aa94707cf29b32",
-                   "traffic": 33_654_272 + 29_440, "warp_inst": 30_243_157},
-    "temperature4096": {"digest": "120d38af0d7a1b4eb54a9e80eb46a3e5110d63251cc6cdfd73aa94707cf29b32",
-                        "traffic": 2_156_800, "warp_inst": 2_189_159},
+    "large16384": {"digest": "a2cffbce1ea01c27649f8bafb5cdd1da61b16e6228b03982ae2545ca52272398",
+                   "traffic": 33_638_400 + 140_288, "warp_inst": 25_808_380},
+    "temperature4096": {"digest": "a2cffbce1ea01c27649f8bafb5cdd1da61b16e6228b03982ae2545ca52272398",
+                        "traffic": 2_158_080, "warp_inst": 1_814_618},
 }
 # What bounds the dominant kernel, from the same captures: the HBM roofline is
 # the algorithm's bound, these are the kernel's.
 PHASE_LIMITER = {
-    "large16384": "integer instruction issue (DRAM throughput 9 %, issue active 62 %, "
-                  "ALU pipe 55 %)",
-    "temperature4096": "latency (issue active 32 %, 3.2 warps a scheduler; one word a thread)",
+    "large16384": "integer instruction issue, then the shared-memory pipe (issue active 61 %, "
+                  "ALU pipe 58 %, shared-memory wavefronts 46 % of peak, half of them bank "
+                  "conflicts of the table lookups; DRAM 11 %)",
+    "temperature4096": "latency: one lattice's phase fills a fifth of the warp slots (warps "
+                       "active 20 %, issue 25 %); the four lattices overlap on their streams",
 }
 # (file, first line, end line): the sources that define the tile phase kernel
 # and its launch -- ccmc_phase.cu from the per-word code through the tile
@@ -213,8 +215,8 @@ def tile_kernel_name(s) -> str:
     152 SMs of a GB300), the pipelined one otherwise."""
     W = (s.Lx // 4 + 15) // 16
     tiles = (s.Ly // 4) // (256 // W)
-    return ("phase_tile_kernel<uint16_t, 5, single>" if tiles <= 5 * 152
-            else "phase_tile_kernel<uint32_t, 4>")
+    return ("phase_tile_kernel<5, true> (one tile per CTA)" if tiles <= 5 * 152
+            else "phase_tile_kernel<4, false> (pipelined tiles)")
 
 
 def _dist():

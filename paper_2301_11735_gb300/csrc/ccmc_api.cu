@@ -17,6 +17,7 @@
 #include "ccmc_internal.h"
 #include "ccmc_map.h"
 #include "ccmc_state.h"
+#include "ccmc_trace.h"
 
 using namespace ccmc;
 
@@ -499,6 +500,7 @@ int ccmc_sweep(ccmc_lattice *h, int64_t nsweeps, double beta, double Delta, doub
     return CCMC_E_INVAL;
   if (!h->initialised) return CCMC_E_STATE;
   if (fault_injected("launch")) return CCMC_E_CUDA;
+  TraceRange trace("ccmc_sweep");
   int rc = upload_params(h, beta, Delta, V, J);
   if (rc) return rc;
   if (nsweeps > 0 && h->phases_done % 8) {
@@ -875,6 +877,7 @@ int batch_run(ccmc_batch *b, const std::vector<ccmc_lattice *> &lats, const int6
               const int *obs_every, bool lockstep) {
   const int n = (int)lats.size();
   if (n > b->cap) return CCMC_E_INVAL;
+  TraceRange trace("ccmc_batch_run");
   for (int i = 0; i < n; ++i) {
     if (nsweeps[i] < 0 || !(beta[i] >= 0.0) || !std::isfinite(Delta[i]) ||
         !std::isfinite(V[i]) || !std::isfinite(J[i]))

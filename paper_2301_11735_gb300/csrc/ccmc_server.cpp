@@ -35,6 +35,7 @@
 #include "../../include/ccmc.h"
 #include "ccmc_fault.h"
 #include "ccmc_internal.h"
+#include "ccmc_trace.h"
 
 namespace {
 
@@ -344,6 +345,7 @@ void ccmc_server::run() {
 
     // (4) the next slice: every active simulation advances by what fits the
     // time budget; those it finishes retire behind it
+    ccmc::TraceRange trace("server slice");
     const int n = (int)active.size();
     std::vector<ccmc_lattice *> lats(n);
     std::vector<int64_t> sw(n);
