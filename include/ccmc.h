@@ -60,11 +60,17 @@ typedef struct {
 
 typedef struct ccmc_lattice ccmc_lattice;
 
-/* Allocate an Lx x Ly lattice on the current CUDA device.  cuda_stream is a
- * cudaStream_t (NULL: the library creates one).  The observable ring holds the
- * last obs_capacity records (<= 0: 4096).  Errors: E_INVAL, E_NOMEM, E_CUDA. */
+/* Allocate an Lx x Ly lattice on the current CUDA device (Lx, Ly multiples of
+ * 4, at least 4, Lx Ly <= 2^30).  cuda_stream is a cudaStream_t (NULL: the
+ * library creates one).  The observable ring holds the last obs_capacity
+ * records (<= 0: 4096).  Device memory comes from a stream-ordered pool the
+ * library keeps per device (allocated and freed in order on the lattice's
+ * stream, cached for reuse until the process exits), so creating and
+ * destroying lattices never synchronises the device.  Returns once the
+ * lattice is ready.  Errors: E_INVAL, E_NOMEM, E_CUDA. */
 int ccmc_lattice_create(int Lx, int Ly, void *cuda_stream, int64_t obs_capacity,
                         ccmc_lattice **out);
+/* Waits for the work queued on the lattice's stream, then releases it. */
 int ccmc_lattice_destroy(ccmc_lattice *h);
 
 /* Constrained initial state (Sec. 3.1, stage 1).  Q = llround(n N);
