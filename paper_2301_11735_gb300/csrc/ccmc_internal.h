@@ -60,8 +60,8 @@ __host__ __device__ inline uint16_t threshold_level(uint32_t thr) {
   return thr == 0xFFFFFFFFu ? (uint16_t)5461 : (uint16_t)(((uint64_t)thr * 5461u) >> 32);
 }
 
-// Move entries: one uint2 per (r, near, pc), entry (2 r + near) * 16 + pc, i.e.
-// at byte offset 256 r + 128 near + 8 pc -- r the pair's choice field mod 12
+// Move entries: one uint2 per (r, near, pc), entry (2 r + near) * 16 + (pc ^ r), i.e.
+// at byte offset 256 r + 128 near + 8 (pc ^ r) -- r the pair's choice field mod 12
 // (12 is a multiple of both q-set sizes, 4 and 6), near whether the partner is a
 // nearest neighbour, pc = 4 code_a + code_b the pair state.
 constexpr int kTransN = 16 * 12;     // entries of one kind (far or near)

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) map_kernel(Geo g, const int32_t *__restri
     r = sl.y % 12u;
   }
   const uint32_t pc = (ca << 2) | cb;
-  const uint2 e = trans[(2u * r + (near ? 1u : 0u)) * 16u + pc];
+  const uint2 e = trans[(2u * r + (near ? 1u : 0u)) * 16u + (pc ^ r)];
   const uint32_t x = (e.y >> 24) & 15u;  // pc XOR the chosen configuration
   if (x == 0u) return;           // the chosen configuration is the current one
   const uint32_t env = (SA + 8u - SB) | (GA << 8) | (GB << 16);

@@ -109,12 +109,17 @@ __device__ __forceinline__ uint32_t window(const uint32_t *cls, const Geo &g, co
   }
 }
 
-// Move entry of choice class r (v mod 12) and pc8 = 8 pc + 128 near: byte
-// offset 256 r + pc8 of the move table.  Word 0: the threshold index's base;
-// word 1: the signed byte coefficients of (D8, GA, GB) and, at bits 24-27 (the
-// byte dp4a multiplies by zero), the move pc XOR npc.
+// Move entry of choice class r (v mod 12) and pc8 = 8 pc + 128 near: entry
+// (2 r + near) 16 + (pc XOR r) of the move table, at byte offset
+// 256 r + 128 near + 8 (pc XOR r) = (264 r) XOR pc8.  The XOR spreads a warp's
+// lookups over the banks: with entry (2 r + near) 16 + pc the bank pair of a
+// lookup was its pair state alone, and the few common states (both sites
+// magnetic) piled onto four of sixteen bank pairs.  Word 0: the threshold
+// index's base; word 1: the signed byte coefficients of (D8, GA, GB) and, at
+// bits 24-27 (the byte dp4a multiplies by zero), the move pc XOR npc.
 __device__ __forceinline__ uint2 move_entry(const uint2 *trans, uint32_t r, uint32_t pc8) {
-  return *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(trans) + r * 256u + pc8);
+  return *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(trans) +
+                                          ((r * 264u) ^ pc8));
 }
 
 // floor(v / 12) for v < 2^16 by a multiply-high: floor(v m / 2^32) with

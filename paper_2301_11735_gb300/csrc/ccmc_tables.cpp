@@ -52,7 +52,7 @@ void build_thresholds(double beta, double Delta, double V, double J, uint32_t *t
 // is an affine function of the biased sums D8 = sum_<a> S - sum_<b> S + 8,
 // GA = sum_<a> sigma + 4, GB = sum_<b> sigma + 4:
 //   index = base + (41 dS_a) D8 + dsig_a GA + dsig_b GB.
-// Entry (2 r + near) * 16 + pc: word 0 holds base; word 1 the signed byte
+// Entry (2 r + near) * 16 + (pc XOR r): word 0 holds base; word 1 the signed byte
 // coefficients (41 dS_a, dsig_a, dsig_b) and, in bits 24-27 (byte 3, which
 // the phase kernel multiplies by zero; bits 28-31 stay clear), pc XOR npc.
 namespace {
@@ -86,7 +86,7 @@ bool build_transitions(uint32_t *trans) {
       const uint32_t coef = ((uint32_t)mulS & 0xFFu) | (((uint32_t)dGa & 0xFFu) << 8) |
                             (((uint32_t)dGb & 0xFFu) << 16) | (x << 24);
       for (int near = 0; near < 2; ++near) {
-        const int e = (2 * r + near) * 16 + pc;
+        const int e = (2 * r + near) * 16 + (pc ^ r);  // bank-spread (see the phase kernel)
         trans[2 * e] = (uint32_t)(near ? near_base : base);
         trans[2 * e + 1] = coef;
       }
