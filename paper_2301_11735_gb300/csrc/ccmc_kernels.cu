@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
   if (threadIdx.x == 0) rec[0] = g.ctl[kCtlPhaseBase] / 8 + a.sweep_off;
   __syncthreads();
   if (threadIdx.x == 0) {
+    rec[3] += bj_completion(g, rec[1]);
     for (int k = 0; k < 8; ++k) g.ctl[kCtlLatest + k] = rec[k];
     if (a.ring) {
       const int64_t cnt = g.ctl[kCtlObsCount];

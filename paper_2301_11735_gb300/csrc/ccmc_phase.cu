@@ -477,7 +477,6 @@ __global__ void __launch_bounds__(256, 4) phase_kernel(Geo g, const uint16_t *th
 constexpr int kTileWords = 256;
 constexpr int kBands = 10;
 constexpr int kTileBufs = 3;
-constexpr int kTileWarps = kTileWords / 32;
 constexpr uint32_t kTileBytes = kBands * kTileWords * 4;
 constexpr uint32_t kWaitSpins = 1u << 24;              // bounded mbarrier waits:
 constexpr unsigned long long kWaitNs = 1000000000ull;  // at most 2^24 polls or 1 s
@@ -570,12 +569,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // One tile-staged phase of lattice g by CTA `cta` of the `ncta` CTAs that
 // work on it; keys: the source of its Philox keys.
 // kSingle: every CTA takes at most one tile (ncta == tiles): one band buffer.
-template <bool kSingle, class Keys>
+// kTPW: threads a word (the CTA has kTileWords kTPW threads; see fast_moves).
+template <bool kSingle, int kTPW, class Keys>
 __device__ __forceinline__ void tile_phase(const Geo &g, const uint16_t *thrT,
                                            const uint32_t *thr32, int64_t p_off, int cta,
                                            int ncta, const Keys &keys) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
   constexpr int kBufs = kSingle ? 1 : kTileBufs;
+  constexpr int kWarps = kTileWords * kTPW / 32;
   using Smem = TileSmem<kBufs>;
   Smem &sm = *reinterpret_cast<Smem *>(tile_smem);
   static_assert(offsetof(Smem, trans) == 2 * kThrT, "tables staged as one block");
@@ -596,16 +597,19 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint16_t *thrT,
     bulk_load(smem_u32(sm.thrT), thrT, kStagedTableBytes, bar);
   }
   // The phase index.  A launch after the first of a chain (p_off > 0) reads the
-  // counter base before it waits for its predecessor: the base was written by
-  // a kernel at least two launches back (the chain's counter advance), which
-  // the predecessor's griddepcontrol.wait has already waited for.  It then
-  // stages the bands of its first tiles that lie in classes the predecessor
-  // (phase P - 1, whose schedule it draws too) does not write, while that
-  // phase is still finishing, and the other bands once it has finished.  Only
-  // lattices whose phases give every CTA several tiles do this: for smaller ones
-  // it measured slower when several lattices share the GPU on their own streams.
-  const bool early = !kSingle && p_off > 0 && g.Cy / (kTileWords / g.W) > ncta;
-  if (!early) {
+  // counter base, draws its schedule and places its bands before it waits for
+  // its predecessor: the base was written by a kernel at least two launches
+  // back (the chain's counter advance), which the predecessor's
+  // griddepcontrol.wait has already waited for.  With several tiles a CTA it
+  // then stages the bands of its first tiles that lie in classes the
+  // predecessor (phase P - 1, whose schedule it draws too) does not write,
+  // while that phase is still finishing, and the other bands once it has
+  // finished.  Only lattices whose phases give every CTA several tiles do
+  // this: for smaller ones it measured slower when several lattices share the
+  // GPU on their own streams.
+  const bool pre = p_off > 0;
+  const bool early = !kSingle && pre && g.Cy / (kTileWords / g.W) > ncta;
+  if (!pre) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
   }
@@ -685,11 +689,16 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint16_t *thrT,
     if (warp == 0)
       for (int i = 0; i < kBufs; ++i)
         if (first_tile(i) >= 0) stage_band(first_tile(i), i, busy);
-  } else if (warp == 0) {
-    for (int i = 0; i < kBufs; ++i) {
-      arm(first_tile(i), i);
-      if (first_tile(i) >= 0) stage_band(first_tile(i), i, (1u << kBands) - 1u);
+  } else {
+    if (pre) {
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      asm volatile("griddepcontrol.launch_dependents;");
     }
+    if (warp == 0)
+      for (int i = 0; i < kBufs; ++i) {
+        arm(first_tile(i), i);
+        if (first_tile(i) >= 0) stage_band(first_tile(i), i, (1u << kBands) - 1u);
+      }
   }
   // phase P - 1 is done (griddepcontrol.wait): tag the claim slot of phase P + 1
   if (!kSingle && cta == 0 && threadIdx.x == 0)
@@ -698,7 +707,8 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint16_t *thrT,
   if (!mbar_wait(smem_u32(&sm.tables), 0u)) sm.err = 1;
 
   const int lw = __ffs(W) - 1;  // W is a power of two
-  const int jr = threadIdx.x >> lw, w = threadIdx.x & (W - 1);
+  const int wi = (int)threadIdx.x / kTPW, sub = (int)threadIdx.x % kTPW;  // word of the tile
+  const int jr = wi >> lw, w = wi & (W - 1);
   // a tile's bands in buffer b as the windows' sources
   auto local_u = [&](int b) {
     const uint32_t *base = sm.band[b][0];
@@ -724,8 +734,8 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint16_t *thrT,
     }
     const int tile = sm.tile[b];
     if (tile < 0) break;
-    warp_word<kRowTile>(g, local_u(b), sm.trans, sm.thrT, thr32, tile * R + jr, jr, w, P, near128,
-                        keys);
+    warp_word<kRowTile, kTPW>(g, local_u(b), sm.trans, sm.thrT, thr32, tile * R + jr, jr, w, P,
+                              near128, keys, sub);
     // (2) this warp is done with the tile: its shared-memory writes are ordered
     // before the async copies that will refill the buffer, and before the
     // last warp's reads
@@ -734,7 +744,7 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint16_t *thrT,
     int last = 0;
     if (lane == 0) {
       __threadfence_block();
-      last = atomicAdd(&sm.done[b], 1) == kTileWarps - 1;
+      last = atomicAdd(&sm.done[b], 1) == kWarps - 1;
       if (last) __threadfence_block();
     }
     last = __shfl_sync(0xFFFFFFFFu, last, 0);
@@ -796,11 +806,12 @@ __device__ __forceinline__ void tile_phase(const Geo &g, const uint16_t *thrT,
 // large-lattice kernel), or five CTAs per SM, one tile per CTA and one band
 // buffer (the compact kernel for lattices whose phase fits one wave: more CTAs
 // resident for several lattices on their own streams, at 48 registers).
-template <int kMinBlocks, bool kSingle>
-__global__ void __launch_bounds__(256, kMinBlocks) phase_tile_kernel(
+template <int kMinBlocks, bool kSingle, int kTPW = 1>
+__global__ void __launch_bounds__(256 * kTPW, kMinBlocks) phase_tile_kernel(
     Geo g, const uint16_t *thrT, const uint32_t *thr32, int64_t p_off,
     const __grid_constant__ RoundKeys rk) {
-  tile_phase<kSingle>(g, thrT, thr32, p_off, (int)blockIdx.x, (int)gridDim.x, TableKeys{&rk});
+  tile_phase<kSingle, kTPW>(g, thrT, thr32, p_off, (int)blockIdx.x, (int)gridDim.x,
+                            TableKeys{&rk});
 }
 
 // Lock-step tile-staged phase of several lattices in one launch: CTAs
@@ -812,8 +823,8 @@ __global__ void __launch_bounds__(256, 4) phase_tile_multi_kernel(const MultiJob
   while (j + 1 < njobs && (int)blockIdx.x >= jobs[j + 1].cta_begin) ++j;
   const MultiJob &J = jobs[j];
   const Geo g = J.g;
-  tile_phase<false>(g, J.thrT, J.thr32, p_off, (int)blockIdx.x - J.cta_begin, J.cta_count,
-                    SeedKeys{g.k0, g.k1});
+  tile_phase<false, 1>(g, J.thrT, J.thr32, p_off, (int)blockIdx.x - J.cta_begin, J.cta_count,
+                       SeedKeys{g.k0, g.k1});
 }
 
 // Lock-step phase of several lattices in one launch: each CTA works on one
@@ -1058,8 +1069,13 @@ int tile_resident_grid() {
   return per_sm * sms;
 }
 
-// CTAs per SM of the single-tile kernel (48 registers; six at 40 registers
-// spilled more and measured slower).
+// The single-tile kernel: one thread a word, five CTAs per SM (48 registers;
+// six at 40 registers spilled more and measured slower).  Two threads a word
+// (512-thread CTAs, two per SM) measured 5.6 us a 4096^2 phase against 5.4,
+// and half the throughput for four such lattices on their own streams: the
+// phase is bound by the issue rate of the SMs that hold two tiles, not by the
+// chain of one thread.
+constexpr int kSmallTPW = 1;
 constexpr int kSmallMinB = 5;
 
 int tile_resident_grid_small() {
@@ -1067,10 +1083,11 @@ int tile_resident_grid_small() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   constexpr int bytes = (int)sizeof(TileSmem<1>);
-  if (cudaFuncSetAttribute(phase_tile_kernel<kSmallMinB, true>,
+  if (cudaFuncSetAttribute(phase_tile_kernel<kSmallMinB, true, kSmallTPW>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_tile_kernel<kSmallMinB, true>, 256,
-                                                    bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, phase_tile_kernel<kSmallMinB, true, kSmallTPW>, 256 * kSmallTPW, bytes) !=
+          cudaSuccess ||
       per_sm < 1 || sms < 1) {
     cudaGetLastError();
     return 0;
@@ -1090,9 +1107,9 @@ cudaError_t launch_phase(const Geo &g, const DevTables &t, int64_t p_off, const 
     // A phase that fits one wave of the compact kernel (one tile per CTA)
     // takes it: measured faster for several such lattices on their own streams.
     if (cfg.tile_grid_small > 0 && tiles <= cfg.tile_grid_small)
-      return launch_pdl_smem(phase_tile_kernel<kSmallMinB, true>, (int)tiles, 256,
-                             sizeof(TileSmem<1>), s, g, (const uint16_t *)t.thrT, t.thr32,
-                             p_off, round_keys(g.k0, g.k1));
+      return launch_pdl_smem(phase_tile_kernel<kSmallMinB, true, kSmallTPW>, (int)tiles,
+                             256 * kSmallTPW, sizeof(TileSmem<1>), s, g,
+                             (const uint16_t *)t.thrT, t.thr32, p_off, round_keys(g.k0, g.k1));
     const int grid = (int)(tiles < cfg.tile_grid ? tiles : cfg.tile_grid);
     return launch_pdl_smem(phase_tile_kernel<4, false>, grid, 256, sizeof(TileSmem<>),
                            s, g, (const uint16_t *)t.thrT, t.thr32, p_off,
