@@ -62,19 +62,19 @@ OBS_EVERY = {"temperature4096": 10, "large16384": 1}
 # They hold only for the kernel sources they were taken with (kernel_digest);
 # after any change to those sources the bench reports them as null.
 PHASE_COUNTERS = {
-    "large16384": {"digest": "a2cffbce1ea01c27649f8bafb5cdd1da61b16e6228b03982ae2545ca52272398",
-                   "traffic": 33_638_400 + 140_288, "warp_inst": 25_808_380},
-    "temperature4096": {"digest": "a2cffbce1ea01c27649f8bafb5cdd1da61b16e6228b03982ae2545ca52272398",
-                        "traffic": 2_158_080, "warp_inst": 1_814_618},
+    "large16384": {"digest": "e6ddb005f8d5ceedad68da55ac243d2d058a839479b6933f3ebea067275a9715",
+                   "traffic": 33_638_144 + 118_528, "warp_inst": 26_336_685},
+    "temperature4096": {"digest": "e6ddb005f8d5ceedad68da55ac243d2d058a839479b6933f3ebea067275a9715",
+                        "traffic": 2_152_960, "warp_inst": 1_906_504},
 }
 # What bounds the dominant kernel, from the same captures: the HBM roofline is
 # the algorithm's bound, these are the kernel's.
 PHASE_LIMITER = {
     "large16384": "integer instruction issue, then the shared-memory pipe (issue active 61 %, "
-                  "ALU pipe 58 %, shared-memory wavefronts 46 % of peak, half of them bank "
+                  "ALU pipe 59 %, shared-memory wavefronts 44 % of peak, half of them bank "
                   "conflicts of the table lookups; DRAM 11 %)",
     "temperature4096": "latency: one lattice's phase fills a fifth of the warp slots (warps "
-                       "active 20 %, issue 25 %); the four lattices overlap on their streams",
+                       "active 21 %, issue 27 %); the four lattices overlap on their streams",
 }
 # (file, first line, end line): the sources that define the tile phase kernel
 # and its launch -- ccmc_phase.cu from the per-word code through the tile
@@ -215,8 +215,8 @@ def tile_kernel_name(s) -> str:
     152 SMs of a GB300), the pipelined one otherwise."""
     W = (s.Lx // 4 + 15) // 16
     tiles = (s.Ly // 4) // (256 // W)
-    return ("phase_tile_kernel<5, true> (one tile per CTA)" if tiles <= 5 * 152
-            else "phase_tile_kernel<4, false> (pipelined tiles)")
+    return ("phase_tile_kernel<5, true, 1> (one tile per CTA)" if tiles <= 5 * 152
+            else "phase_tile_kernel<4, false, 1> (pipelined tiles)")
 
 
 def _dist():
