@@ -83,7 +83,7 @@ struct RecountArgs {
 };
 
 // Grid (gx, 16): grid row y counts class y.
-__global__ void __launch_bounds__(256) recount_kernel(Geo g, RecountArgs a) {
+__global__ void __launch_bounds__(256, 5) recount_kernel(Geo g, RecountArgs a) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
   int c[7] = {0, 0, 0, 0, 0, 0, 0};  // Nc, BV, BJ, M, Ms, S, Ss
@@ -335,11 +335,13 @@ cudaError_t launch_init(const Geo &g, int h, int64_t n_plus, int64_t n_minus, cu
 }
 
 // Grid x-extent of recount_kernel (its y-extent is the 16 classes): at most
-// 16 x 38 = 608 blocks, one wave at four blocks per SM.  A thread's unit is a
-// word, or four words on rows that allow 16-byte loads.
+// 16 x 47 = 752 blocks, one wave at five blocks per SM (48 registers: the
+// quad loop keeps two quads' loads in flight a thread; on four blocks per SM
+// it measured 1 % slower at 16384^2).  A thread's unit is a word, or four
+// words on rows that allow 16-byte loads.
 static int recount_gx(const Geo &g) {
   const int64_t units = (int64_t)g.Cy * g.W / (((g.Cx & 15) == 0 && (g.W & 3) == 0) ? 4 : 1);
-  return grid_for(units, 256, 38);
+  return grid_for(units, 256, 47);
 }
 
 int recount_grid(const Geo &g) { return 16 * recount_gx(g); }
