@@ -133,31 +133,6 @@ constexpr uint32_t kLutAnd3 = 0x80;     // a & b & c
 constexpr uint32_t kLutNorAnd = 0x02;   // ~(a | b) & c
 constexpr uint32_t kLutAndNot = 0x0C;   // ~a & b
 
-// One quad's inputs: four words of a class row, the right and down neighbour
-// windows' words, and the word after the right ones (class column 3 only).
-struct QuadIn {
-  uint4 x, r, d;
-  uint32_t rn;
-};
-
-template <bool kColR, bool kRowD>
-__device__ __forceinline__ QuadIn load_quad(const uint32_t *__restrict__ X0,
-                                            const uint32_t *__restrict__ R0,
-                                            const uint32_t *__restrict__ D0, int W, int q, int wq,
-                                            int last_row) {
-  QuadIn in;
-  const int o = 4 * q;  // word offset of the quad: row j, column 4 wq
-  // the down neighbours of class row Cy-1 of the last class row wrap to row 0
-  const int od = kRowD ? (q < last_row ? o + W : o - last_row * 4) : o;
-  in.x = *reinterpret_cast<const uint4 *>(X0 + o);
-  in.r = *reinterpret_cast<const uint4 *>(R0 + o);
-  in.d = *reinterpret_cast<const uint4 *>(D0 + od);
-  // right neighbours of class column 3 are one column further on: the
-  // windows start one site later (the last one wraps to the row's start)
-  in.rn = kColR ? R0[wq == (W >> 2) - 1 ? o + 4 - W : o + 4] : 0u;
-  return in;
-}
-
 template <bool kColR, bool kRowD>
 __device__ __forceinline__ void count_quads(const uint32_t *__restrict__ X0,
                                             const uint32_t *__restrict__ R0,
@@ -165,23 +140,27 @@ __device__ __forceinline__ void count_quads(const uint32_t *__restrict__ X0,
                                             int q, int nthreads, QuadCounts &n) {
   constexpr uint32_t kOdd = 0xAAAAAAAAu;
   const int Wq = W >> 2, nq = Cy * Wq, last_row = (Cy - 1) * Wq;
-  if (q >= nq) return;
   int wq = q % Wq;
   const int sw = nthreads % Wq;
-  // software-pipelined: the next quad's loads are issued before this quad is
-  // counted, so two quads' loads are in flight a thread
-  QuadIn cur = load_quad<kColR, kRowD>(X0, R0, D0, W, q, wq, last_row);
-#pragma unroll 1
-  for (;;) {
-    const int qn = q + nthreads;
-    int wqn = wq + sw;
-    if (wqn >= Wq) wqn -= Wq;
-    const bool more = qn < nq;
-    QuadIn nxt{};
-    if (more) nxt = load_quad<kColR, kRowD>(X0, R0, D0, W, qn, wqn, last_row);
-    const uint32_t xs[4] = {cur.x.x, cur.x.y, cur.x.z, cur.x.w};
-    const uint32_t ds[4] = {cur.d.x, cur.d.y, cur.d.z, cur.d.w};
-    const uint32_t rs[5] = {cur.r.x, cur.r.y, cur.r.z, cur.r.w, cur.rn};
+#pragma unroll 2
+  for (; q < nq; q += nthreads) {
+    const int o = 4 * q;  // word offset of the quad: row j, column 4 wq
+    // the down neighbours of class row Cy-1 of the last class row wrap to row 0
+    const int od = kRowD ? (q < last_row ? o + W : o - last_row * 4) : o;
+    const uint4 x = *reinterpret_cast<const uint4 *>(X0 + o);
+    const uint4 r = *reinterpret_cast<const uint4 *>(R0 + o);
+    const uint4 d = *reinterpret_cast<const uint4 *>(D0 + od);
+    // right neighbours of class column 3 are one column further on: the
+    // windows start one site later (the last one wraps to the row's start)
+    uint32_t rn = 0u;
+    if (kColR) {
+      rn = R0[wq == Wq - 1 ? o + 4 - W : o + 4];
+      wq += sw;
+      if (wq >= Wq) wq -= Wq;
+    }
+    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+    const uint32_t ds[4] = {d.x, d.y, d.z, d.w};
+    const uint32_t rs[5] = {r.x, r.y, r.z, r.w, rn};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const uint32_t X = xs[k], Yd = ds[k];
@@ -204,10 +183,6 @@ __device__ __forceinline__ void count_quads(const uint32_t *__restrict__ X0,
       n.nUG += __popc(lop3<kLutAndNot>(T, S, 0u));
     }
     ++n.quads;
-    if (!more) break;
-    cur = nxt;
-    q = qn;
-    wq = wqn;
   }
 }
 

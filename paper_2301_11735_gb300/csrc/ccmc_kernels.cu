@@ -335,10 +335,8 @@ cudaError_t launch_init(const Geo &g, int h, int64_t n_plus, int64_t n_minus, cu
 }
 
 // Grid x-extent of recount_kernel (its y-extent is the 16 classes): at most
-// 16 x 47 = 752 blocks, one wave at five blocks per SM (48 registers: the
-// quad loop keeps two quads' loads in flight a thread; on four blocks per SM
-// it measured 1 % slower at 16384^2).  A thread's unit is a word, or four
-// words on rows that allow 16-byte loads.
+// 16 x 47 = 752 blocks, one wave at five blocks per SM (48 registers).  A
+// thread's unit is a word, or four words on rows that allow 16-byte loads.
 static int recount_gx(const Geo &g) {
   const int64_t units = (int64_t)g.Cy * g.W / (((g.Cx & 15) == 0 && (g.W & 3) == 0) ? 4 : 1);
   return grid_for(units, 256, 47);
