@@ -8,7 +8,8 @@ thread evaluates, 16, 8 or 4).  None of them changes results -- the random
 streams are keyed by (seed, phase, site) -- so the tuner may pick freely.
 
 A probe batch of synthetic lattices with the same shapes is swept for a few
-sweeps under every candidate; the fastest candidate is cached in a JSON file
+sweeps under every candidate, twice (the faster probe counts); the fastest
+candidate is cached in a JSON file
 (paper_2301_11735_gb300/_build/autotune.json) keyed by the GPU name and the
 batch's shape signature.
 """
@@ -89,10 +90,13 @@ def tune(shapes, probe_sweeps: int = 20, params=(1.0, 0.0, 1.0, 1.0), use_cache:
                 continue
             b.sweep(2, *params)  # warm-up
             b.sync()
-            t0 = time.perf_counter()
-            b.sweep(probe_sweeps, *params)
-            b.sync()
-            timings[cand] = time.perf_counter() - t0
+            best = float("inf")
+            for _ in range(2):  # the faster of two probes: one noisy probe picked a slower shape
+                t0 = time.perf_counter()
+                b.sweep(probe_sweeps, *params)
+                b.sync()
+                best = min(best, time.perf_counter() - t0)
+            timings[cand] = best
     for lat in lats:
         lat.close()
     if not timings:
