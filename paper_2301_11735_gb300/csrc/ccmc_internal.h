@@ -88,6 +88,8 @@ struct JobDesc {
   int obs_every;
   int max_tpw;              // threads a word: the most of 4, 2, 1 (at most max_tpw) that
                             // take a phase's words in one pass of the CTA, else 1
+  int warp;                 // 1: run by one warp of a CTA, the lattice in that warp's
+                            // share of the shared memory (the launch's warp_words)
 };
 
 // One lattice of a lock-step multi-lattice phase launch: CTAs
@@ -136,9 +138,15 @@ cudaError_t launch_set_ctl(int64_t *ctl, int64_t phase_base, cudaStream_t s);
 cudaError_t launch_unpack(const Geo &g, uint8_t *out, cudaStream_t s);
 cudaError_t launch_pack(const Geo &g, const uint8_t *in, int *bad, cudaStream_t s);
 // Resident batch kernel: grid CTAs of `threads` threads take jobs from *queue
-// (zeroed by the caller) until njobs are done; max_words bounds 16 Cy W.
+// (zeroed by the caller) until njobs are done; max_words bounds 16 Cy W of
+// the jobs a whole CTA runs.  Jobs with `warp` set come last in d_jobs and
+// have 16 Cy W <= resident_warp_words(threads, max_words).
 cudaError_t launch_resident(const JobDesc *d_jobs, int njobs, int *d_queue, int grid, int threads,
                             int64_t max_words, cudaStream_t s);
+// Words of one warp's share of a resident CTA's shared memory, and the
+// resident CTAs of `threads` threads an SM holds at once.
+int64_t resident_warp_words(int threads, int64_t max_words);
+int resident_ctas_per_sm(int threads, int64_t max_words);
 int64_t resident_smem_bytes(int64_t max_words);
 cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                           uint32_t k1, int64_t count, uint32_t *out, cudaStream_t s);

@@ -870,6 +870,103 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
   }
 }
 
+// One lattice run by one warp of a resident CTA (JobDesc.warp): its words in
+// the warp's share of the shared memory, its tables read through L1 from
+// global memory, the warp's own barrier between phases.  The same per-word
+// code as the CTA path, so results are identical.
+template <int kMode, int kTPW>
+__device__ __forceinline__ void warp_job_phase(const Geo &gs, const PhaseU &u, const uint2 *trans,
+                                               const uint16_t *thrT, const uint32_t *thr32,
+                                               int nwa, uint64_t P, uint32_t near128) {
+  const int lane = threadIdx.x & 31;
+  const SeedKeys keys{gs.k0, gs.k1};
+  for (int base = 0; base < kTPW * nwa; base += 32) {  // uniform trip count
+    const int i = base + lane;
+    const bool act = i < kTPW * nwa;
+    const int wid = !act ? 0 : (kTPW == 1 ? i : (kTPW == 2 ? i >> 1 : i >> 2));
+    const int sub = act ? i - kTPW * wid : 0;
+    const int j = wid / gs.W, w = wid - j * gs.W;
+    warp_word<kMode, kTPW>(gs, u, trans, thrT, thr32, j, j, w, P, near128, keys, sub, act);
+  }
+}
+
+__device__ __forceinline__ void warp_job(const JobDesc &J, uint32_t *region, PhaseU &su) {
+  const int lane = threadIdx.x & 31;
+  const Geo g = J.g;
+  const int64_t nw = 16 * g.cstride;
+  for (int64_t t = lane; t < nw; t += 32) region[t] = g.words[t];
+  const int64_t P0 = g.ctl[kCtlPhaseBase];
+  const int64_t nsweeps = J.nsweeps;
+  const int obs_every = J.obs_every;
+  Geo gs = g;
+  gs.words = region;
+  const bool aligned = (g.Cx & 15) == 0;
+  const int nwa = g.Cy * g.W;  // a-words per phase
+  const int tpw = J.max_tpw >= 4 && 4 * nwa <= 32 ? 4 : J.max_tpw >= 2 && 2 * nwa <= 32 ? 2 : 1;
+  const uint2 *trans = reinterpret_cast<const uint2 *>(J.trans);
+  int64_t obs_cnt = 0, obs_slot = 0;
+  if (lane == 0 && obs_every > 0) {
+    obs_cnt = g.ctl[kCtlObsCount];
+    obs_slot = obs_cnt % J.ring_cap;
+  }
+  __syncwarp();
+  for (int64_t s = 0; s < nsweeps; ++s) {
+    for (int p = 0; p < 8; ++p) {
+      const uint64_t P = (uint64_t)(P0 + 8 * s + p);
+      const Sched sc = draw_schedule(gs, P);
+      if (lane == 0) su = phase_uniform(gs, sc);
+      __syncwarp();
+      const PhaseU &u = su;  // read from shared memory where used
+      const uint32_t near128 = sc.near ? 128u : 0u;
+      if (aligned) {
+        if (tpw == 1)
+          warp_job_phase<kRowAligned, 1>(gs, u, trans, J.thrT, J.thr32, nwa, P, near128);
+        else if (tpw == 2)
+          warp_job_phase<kRowAligned, 2>(gs, u, trans, J.thrT, J.thr32, nwa, P, near128);
+        else
+          warp_job_phase<kRowAligned, 4>(gs, u, trans, J.thrT, J.thr32, nwa, P, near128);
+      } else {
+        if (tpw == 1)
+          warp_job_phase<kRowGeneral, 1>(gs, u, trans, J.thrT, J.thr32, nwa, P, near128);
+        else if (tpw == 2)
+          warp_job_phase<kRowGeneral, 2>(gs, u, trans, J.thrT, J.thr32, nwa, P, near128);
+        else
+          warp_job_phase<kRowGeneral, 4>(gs, u, trans, J.thrT, J.thr32, nwa, P, near128);
+      }
+      __syncwarp();  // the phase's writes before the next phase's reads
+    }
+    const int64_t done = P0 / 8 + s + 1;
+    if (obs_every > 0 && done % obs_every == 0) {
+      // the 16 classes side by side, two lanes a class
+      int c[7] = {0, 0, 0, 0, 0, 0, 0};
+      count_class(gs, lane >> 1, lane & 1, 2, c);
+      int64_t rec[8];
+      rec[0] = done;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) rec[1 + k] = warp_sum((int64_t)c[k]);
+      if (lane == 0) {
+        for (int k = 0; k < 8; ++k) g.ctl[kCtlLatest + k] = rec[k];
+        int64_t *dst = J.ring + obs_slot * 8;
+        for (int k = 0; k < 8; ++k) dst[k] = rec[k];
+        g.ctl[kCtlObsCount] = ++obs_cnt;
+        if (++obs_slot == J.ring_cap) obs_slot = 0;
+        if (J.hist) {
+          const int64_t N = (int64_t)g.Lx * g.Ly;
+          const int64_t vals[3] = {rec[4], rec[5], rec[7]};
+          for (int h = 0; h < 3; ++h)
+            atomicAdd(reinterpret_cast<unsigned long long *>(
+                          J.hist + h * J.nbins + (vals[h] + N) * J.nbins / (2 * N + 1)),
+                      1ull);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  for (int64_t t = lane; t < nw; t += 32) g.words[t] = region[t];
+  if (lane == 0) g.ctl[kCtlPhaseBase] = P0 + 8 * nsweeps;
+  __syncwarp();
+}
+
 // ============================================================================
 // Resident batch kernel (many lattices of uneven size, one persistent launch).
 // Each CTA takes lattices from a work queue, largest first; it holds the whole
@@ -879,7 +976,7 @@ __global__ void __launch_bounds__(256, 4) phase_multi_kernel(const MultiJob *__r
 // per-word code as phase_kernel runs against shared memory, so results are
 // identical to the per-phase launches.
 __global__ void __launch_bounds__(512, 1) resident_kernel(const JobDesc *__restrict__ jobs, int njobs,
-                                                       int *queue) {
+                                                       int *queue, int warp_words) {
   extern __shared__ __align__(16) uint32_t dyn[];
   uint16_t *s_thrT = reinterpret_cast<uint16_t *>(dyn);
   uint2 *s_trans = reinterpret_cast<uint2 *>(dyn + kThrT / 2);
@@ -888,12 +985,31 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const JobDesc *__restr
   __shared__ PhaseU s_u[8];     // and their class pointers and offsets
   __shared__ int s_job;
   __shared__ int64_t s_red[32][7];
+  __shared__ PhaseU s_wu[16];  // one-warp jobs: each warp's current phase
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
     if (threadIdx.x == 0) s_job = atomicAdd(queue, 1);
     __syncthreads();
     const int job = s_job;
     if (job >= njobs) break;
+    if (jobs[job].warp) {
+      // the rest of the queue is one-warp jobs (the planner orders them
+      // last): every warp takes its own from here on, warp 0 this one
+      uint32_t *region = dyn + (int64_t)warp * warp_words;
+      for (int jw = warp == 0 ? job : -1;;) {
+        if (jw < 0) {
+          int x = 0;
+          if (lane == 0) x = atomicAdd(queue, 1);
+          jw = __shfl_sync(0xFFFFFFFFu, x, 0);
+        }
+        if (jw >= njobs) return;
+        if (jobs[jw].warp && 16 * jobs[jw].g.cstride <= warp_words)
+          warp_job(jobs[jw], region, s_wu[warp]);
+        else if (lane == 0)
+          jobs[jw].g.ctl[kCtlStatus] = 1;  // not a one-warp job: the planner's order broke
+        jw = -1;
+      }
+    }
     const JobDesc &J = jobs[job];
     const Geo g = J.g;
     const int64_t nw = 16 * g.cstride;
@@ -1018,13 +1134,31 @@ int64_t resident_smem_bytes(int64_t max_words) {
   return (int64_t)sizeof(uint32_t) * (kResTableWords + max_words);
 }
 
+int resident_ctas_per_sm(int threads, int64_t max_words) {
+  const int smem = (int)resident_smem_bytes(max_words);
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel, threads, smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+int64_t resident_warp_words(int threads, int64_t max_words) {
+  return ((kResTableWords + max_words) / (threads / 32)) & ~(int64_t)3;
+}
+
 cudaError_t launch_resident(const JobDesc *d_jobs, int njobs, int *d_queue, int grid, int threads,
                             int64_t max_words, cudaStream_t s) {
   const int64_t smem = resident_smem_bytes(max_words);
   cudaError_t e = cudaFuncSetAttribute(resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  resident_kernel<<<grid, threads, (size_t)smem, s>>>(d_jobs, njobs, d_queue);
+  resident_kernel<<<grid, threads, (size_t)smem, s>>>(
+      d_jobs, njobs, d_queue, (int)resident_warp_words(threads, max_words));
   return cudaGetLastError();
 }
 

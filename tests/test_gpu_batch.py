@@ -77,6 +77,23 @@ def test_batch_equals_individual_sweeps_and_oracle(cc):
         assert np.array_equal(got[i][0], st) and np.array_equal(got[i][1], rec), MIX[i]
 
 
+# More lattices than CTAs resident at once (one CTA an SM): those whose words
+# fit one warp's share of the CTA's shared memory run one a warp.
+PACKED = [(4, 4), (8, 12), (16, 16), (20, 12), (32, 32), (36, 44), (64, 64), (68, 20),
+          (128, 128), (12, 40)]
+
+
+@pytest.mark.parametrize("cfg", [(256, 1 << 17, 1, 4), (512, 1 << 17, 1, 2), (64, 1 << 17, 1, 1)])
+def test_many_small_lattices_run_one_a_warp_bit_exact(cc, cfg):
+    shapes = [PACKED[i % len(PACKED)] for i in range(200)]
+    nsw = [5 + i % 7 for i in range(200)]
+    got = _run_batch(cc, shapes, nsw, obs_every=3, cfg=cfg)
+    ref = _run_single(cc, shapes, nsw, obs_every=3)
+    for i, ((s1, r1), (s2, r2)) in enumerate(zip(got, ref)):
+        assert np.array_equal(s1, s2), (cfg, i, shapes[i])
+        assert np.array_equal(r1, r2), (cfg, i, shapes[i])
+
+
 @pytest.mark.parametrize("cfg", [(64, 1 << 17, 1, 4), (128, 1 << 17, 4, 4), (256, 1 << 17, 8, 4),
                                  (256, 4096, 2, 4), (256, 1 << 17, 2, 1), (256, 1 << 17, 2, 2),
                                  (512, 1 << 17, 1, 1), (512, 1 << 17, 1, 2),
